@@ -1,0 +1,161 @@
+/*
+ * glv.h -- C ABI of the GB300 (sm_103a) GleanVec eager search library (libglv.so).
+ *
+ * GleanVec (arXiv 2410.22347, Section 4) approximates the inner product of a query q and a
+ * database vector x_i by <A_{c_i} q, B_{c_i} x_i>, where c_i is the vector's cluster tag
+ * (Eq. cluster_tag) and (A_c, B_c) are per-cluster d x D reduction matrices.  The eager
+ * variant (Algorithm 4) projects every query through all C matrices once and then scores
+ * each candidate by one d-long dot product against the projected query of its cluster.
+ * Search follows the multi-step scheme of Algorithm 1: score the candidates in the
+ * reduced space, keep the best kappa, re-rank them exactly in full dimension D, return k.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Every array argument is a DEVICE pointer owned by the caller; the library never
+ *    allocates, frees or retains it.  Matrices are row-major.
+ *  * `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Every
+ *    call enqueues work on that stream and returns without synchronising.
+ *  * Arguments are validated on the host before anything is enqueued; an invalid argument
+ *    returns GLV_ERR_INVALID_ARG (or GLV_ERR_UNSUPPORTED for a legal shape this build does
+ *    not handle) and nothing is enqueued.  A failed launch returns GLV_ERR_CUDA.
+ *  * Errors only the device can see (a candidate / survivor id outside [0, N), a tag
+ *    outside [0, C)) are written into the caller-provided device word `d_status` (may be
+ *    NULL): the first error code wins, later ones are dropped, and the offending item is
+ *    skipped (its score is -inf).  Clear the word to GLV_OK before the call and read it
+ *    back after synchronising the stream.
+ *  * Orderings: results are sorted by score descending, ties broken by the smaller id;
+ *    NaN scores rank after every number; a slot with no candidate holds id -1 and score
+ *    -inf.
+ *  * Sizes: N < 2^31 database rows (ids are int32), 1 <= C <= 65536 clusters (tags are
+ *    uint16), 1 <= d <= D.
+ */
+#ifndef GLV_H_
+#define GLV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GLV_OK = 0,
+  GLV_ERR_INVALID_ARG = 1, /* bad pointer / size / alignment; nothing enqueued          */
+  GLV_ERR_BAD_ID = 2,      /* (device word) an id or tag was out of range; item skipped */
+  GLV_ERR_UNSUPPORTED = 3, /* legal shape outside what this build handles               */
+  GLV_ERR_CUDA = 4,        /* a CUDA runtime call or a launch failed                    */
+  GLV_ERR_TIMEOUT = 5      /* (device word) a bounded device-side wait ran out          */
+} glv_status;
+
+/* Storage type of the reduced rows x_i^low (and compute type of the projection).
+ * Section 2.1 says the reduced vectors may be scalar-quantised "as in LeanVec" without
+ * fixing a scheme; this library offers:
+ *   GLV_F32      : FP32 values.
+ *   GLV_BF16     : bfloat16, round-to-nearest-even of the FP32 value.
+ *   GLV_FP8_E4M3 : OCP FP8 e4m3 codes with one FP32 scale per row,
+ *                  s_i = max_j |x_ij| / 448, code_ij = RNE_e4m3(x_ij / s_i) saturating;
+ *                  the represented value is s_i * decode(code_ij). */
+typedef enum { GLV_F32 = 0, GLV_BF16 = 1, GLV_FP8_E4M3 = 2 } glv_dtype;
+
+#define GLV_ABI_VERSION 1
+#define GLV_MAX_KAPPA 1024 /* largest kappa accepted by glv_topk / glv_rerank */
+
+int32_t glv_abi_version(void);
+const char* glv_status_string(glv_status s);
+
+/* Smallest legal row stride in bytes of a reduced-row store of width d and type dt:
+ * d * sizeof(element) rounded up to 16 bytes (rows are read with 16-byte vector loads). */
+int64_t glv_min_row_stride(int32_t d, glv_dtype dt);
+
+/* ---------------------------------------------------------------------------------------
+ * Cluster tags, Eq. (cluster_tag), Section 4:  c_i = argmax_c <x_i, mu_c>.
+ *   X    : N x D float32, rows contiguous.
+ *   mu   : C x D float32 landmarks.
+ *   tags : N uint16 output.  Ties go to the lowest c.  FP32 accumulation.
+ * Limits: C * D * 4 bytes must fit in shared memory (C * D <= 49152).
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_assign_tags(const float* X, int64_t N, int32_t D, const float* mu, int32_t C,
+                           uint16_t* tags, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Reduced database, Eq. (X_low), Section 4, read as x_i^low = g_{c_i}(x_i) = B_{c_i} x_i
+ * (the equation prints f; the GleanVec approximation that follows it and the definition
+ * g_c(x) = B_c x fix g).  Rows are grouped by cluster on the device and each group is
+ * multiplied by its B_c (a grouped GEMM, FP32 accumulation); the epilogue stores the
+ * row in `dt` (see glv_dtype).
+ *   X          : N x D float32.            tags : N uint16, each < C.
+ *   B          : C x d x D float32 (B_c row-major, clusters consecutive).
+ *   Xred       : N rows of `row_stride` bytes; row i holds d elements of type `dt`,
+ *                then zero bytes up to the next 16-byte boundary.  16-byte aligned.
+ *   row_stride : multiple of 16, >= glv_min_row_stride(d, dt).
+ *   scales     : N float32 per-row scales (FP8 only; must be NULL otherwise).
+ *   workspace  : device scratch of glv_build_reduced_workspace_size(N, C) bytes,
+ *                256-byte aligned; its contents on entry do not matter.
+ *   d_status   : optional device error word (tag >= C -> GLV_ERR_BAD_ID, row skipped).
+ * ------------------------------------------------------------------------------------- */
+size_t glv_build_reduced_workspace_size(int64_t N, int32_t C);
+glv_status glv_build_reduced(const float* X, int64_t N, int32_t D, const uint16_t* tags,
+                             const float* B, int32_t C, int32_t d, glv_dtype dt, void* Xred,
+                             int64_t row_stride, float* scales, void* workspace,
+                             int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Query preprocessing of Algorithm 4 (eager):  q_{j,c} = A_c q_j  for every c = 1..C,
+ * i.e. one dense GEMM  Qp = Q . [A_1; ...; A_C]^T  of shape nq x (C*d).
+ *   Q       : nq x D float32.           A : C x d x D float32.
+ *   compute : GLV_F32 -- FP32 products and sums (matches an FP64 reference to ~1e-6
+ *             relative); GLV_BF16 -- operands rounded to bfloat16, FP32 accumulation.
+ *   Qp      : nq x C x d float32 output (row j holds the C projected views of q_j).
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_project_queries(const float* Q, int64_t nq, int32_t D, const float* A,
+                               int32_t C, int32_t d, glv_dtype compute, float* Qp,
+                               void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Candidate scoring, Algorithm 4 procedure inner-product and Eq. (GleanVec approximation):
+ * for query j and each candidate id i in its list,
+ *        s = <q_{j, c_i}, x_i^low>        (times s_i for FP8 rows),
+ * FP32 accumulation.  Candidate lists are CSR: list j is
+ * cand_ids[cand_off[j] .. cand_off[j+1]); they stand in for the vertices a graph search
+ * visits (Algorithm 1, main step).
+ *   Qp        : nq x C x d float32 (from glv_project_queries).
+ *   Xred, row_stride, scales, dt : the store written by glv_build_reduced.
+ *   tags      : N uint16.   cand_off : nq+1 int64, non-decreasing, cand_off[0] = 0.
+ *   cand_ids  : int32 ids; an id outside [0, N) scores -inf and sets GLV_ERR_BAD_ID.
+ *   scores    : cand_off[nq] float32 output, aligned with cand_ids.
+ * Limits: C * d <= 49152 (one query's C projected views are staged in shared memory).
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_score_candidates(const float* Qp, int64_t nq, int32_t C, int32_t d,
+                                const void* Xred, int64_t row_stride, const float* scales,
+                                glv_dtype dt, const uint16_t* tags, int64_t N,
+                                const int64_t* cand_off, const int32_t* cand_ids,
+                                float* scores, int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Per-query top-kappa of the scores (Algorithm 1: the main step hands kappa candidates to
+ * the post-processing).  Exact selection (radix select on order-preserving keys), output
+ * sorted by score descending, ties to the smaller id, NaN last, padding (-inf, -1) when a
+ * list has fewer than kappa entries.
+ *   scores, cand_off, cand_ids : as for glv_score_candidates.
+ *   out_s, out_id : nq x kappa float32 / int32 outputs.     1 <= kappa <= GLV_MAX_KAPPA.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_topk(const float* scores, const int64_t* cand_off, const int32_t* cand_ids,
+                    int64_t nq, int32_t kappa, float* out_s, int32_t* out_id, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Post-processing of Algorithm 1: exact inner products <q_j, x_i> in full dimension D
+ * (FP32 accumulation) for each query's survivors, then the top k of them.
+ *   X      : N x D float32.   Q : nq x D float32.
+ *   surv_id: nq x kappa int32; -1 marks an empty slot; another id outside [0, N) is
+ *            skipped and sets GLV_ERR_BAD_ID.
+ *   out_s, out_id : nq x k outputs.   1 <= k <= kappa <= GLV_MAX_KAPPA.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_rerank(const float* X, int64_t N, int32_t D, const float* Q, int64_t nq,
+                      const int32_t* surv_id, int32_t kappa, int32_t k, float* out_s,
+                      int32_t* out_id, int32_t* d_status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLV_H_ */

@@ -1,0 +1,185 @@
+// api.cu -- the extern "C" entry points declared in include/glv.h: host-side validation
+// (before anything is enqueued) and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace glv {
+
+constexpr size_t kSmemLimit = 227 * 1024;  // opt-in dynamic shared memory per CTA (sm_100+)
+constexpr int64_t kMaxGridX = 2147483647;
+
+static int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  return n;
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+static int elem_bytes(int dt) { return dt == GLV_F32 ? 4 : (dt == GLV_BF16 ? 2 : 1); }
+static bool valid_dt(int dt) { return dt == GLV_F32 || dt == GLV_BF16 || dt == GLV_FP8_E4M3; }
+
+}  // namespace glv
+
+using namespace glv;
+
+#define GLV_CHECK(cond, code) \
+  do {                        \
+    if (!(cond)) return code; \
+  } while (0)
+
+#define GLV_LAUNCH(expr)                            \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return GLV_ERR_CUDA;     \
+  } while (0)
+
+extern "C" {
+
+int32_t glv_abi_version(void) { return GLV_ABI_VERSION; }
+
+const char* glv_status_string(glv_status s) {
+  switch (s) {
+    case GLV_OK: return "ok";
+    case GLV_ERR_INVALID_ARG: return "invalid argument";
+    case GLV_ERR_BAD_ID: return "id or tag out of range";
+    case GLV_ERR_UNSUPPORTED: return "unsupported shape";
+    case GLV_ERR_CUDA: return "CUDA error";
+    case GLV_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+int64_t glv_min_row_stride(int32_t d, glv_dtype dt) {
+  if (d <= 0 || !valid_dt(dt)) return -1;
+  return ((int64_t)d * elem_bytes(dt) + 15) / 16 * 16;
+}
+
+glv_status glv_assign_tags(const float* X, int64_t N, int32_t D, const float* mu, int32_t C,
+                           uint16_t* tags, void* stream) {
+  GLV_CHECK(N >= 0 && D >= 1 && C >= 1 && C <= 65536, GLV_ERR_INVALID_ARG);
+  if (N == 0) return GLV_OK;
+  GLV_CHECK(X && mu && tags, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(D <= 1024 && (size_t)C * D * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
+  GLV_LAUNCH(launch_tags(X, N, D, mu, C, tags, num_sms(), (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+size_t glv_build_reduced_workspace_size(int64_t N, int32_t C) {
+  if (N < 0 || C < 1) return 0;
+  return build_ws_bytes(N, C);
+}
+
+glv_status glv_build_reduced(const float* X, int64_t N, int32_t D, const uint16_t* tags,
+                             const float* B, int32_t C, int32_t d, glv_dtype dt, void* Xred,
+                             int64_t row_stride, float* scales, void* workspace,
+                             int32_t* d_status, void* stream) {
+  GLV_CHECK(N >= 0 && N <= 2147483647LL, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(D >= 1 && C >= 1 && C <= 65536 && d >= 1 && d <= D && valid_dt(dt),
+            GLV_ERR_INVALID_ARG);
+  GLV_CHECK(row_stride >= glv_min_row_stride(d, dt) && row_stride % 16 == 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK((dt == GLV_FP8_E4M3) == (scales != nullptr), GLV_ERR_INVALID_ARG);
+  if (N == 0) return GLV_OK;
+  GLV_CHECK(X && tags && B && Xred && workspace, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(aligned(Xred, 16) && aligned(workspace, 256), GLV_ERR_INVALID_ARG);
+  GLV_CHECK((size_t)32 * ((d + 3) & ~3) * 4 <= kSmemLimit - 16 * 1024, GLV_ERR_UNSUPPORTED);
+  GLV_CHECK((N + 31) / 32 + C <= kMaxGridX, GLV_ERR_UNSUPPORTED);
+  GLV_LAUNCH(launch_build(X, N, D, tags, B, C, d, dt, Xred, row_stride, scales, workspace,
+                          d_status, (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_project_queries(const float* Q, int64_t nq, int32_t D, const float* A,
+                               int32_t C, int32_t d, glv_dtype compute, float* Qp,
+                               void* stream) {
+  GLV_CHECK(nq >= 0 && D >= 1 && C >= 1 && C <= 65536 && d >= 1 && d <= D, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(compute == GLV_F32 || compute == GLV_BF16, GLV_ERR_INVALID_ARG);
+  if (nq == 0) return GLV_OK;
+  GLV_CHECK(Q && A && Qp, GLV_ERR_INVALID_ARG);
+  const int64_t M = (int64_t)C * d;
+  GLV_CHECK(M <= 2147483647LL && nq <= 65535LL * 128, GLV_ERR_UNSUPPORTED);
+  if (compute == GLV_BF16) return GLV_ERR_UNSUPPORTED;  // tensor-core path not in this build
+  GLV_LAUNCH(launch_project_simt(Q, nq, D, A, M, Qp, (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_score_candidates(const float* Qp, int64_t nq, int32_t C, int32_t d,
+                                const void* Xred, int64_t row_stride, const float* scales,
+                                glv_dtype dt, const uint16_t* tags, int64_t N,
+                                const int64_t* cand_off, const int32_t* cand_ids,
+                                float* scores, int32_t* d_status, void* stream) {
+  GLV_CHECK(nq >= 0 && C >= 1 && C <= 65536 && d >= 1 && N >= 0 && valid_dt(dt),
+            GLV_ERR_INVALID_ARG);
+  GLV_CHECK(row_stride >= glv_min_row_stride(d, dt) && row_stride % 16 == 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK((dt == GLV_FP8_E4M3) == (scales != nullptr), GLV_ERR_INVALID_ARG);
+  if (nq == 0) return GLV_OK;
+  GLV_CHECK(Qp && cand_off && tags && Xred && cand_ids && scores, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(aligned(Xred, 16), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(nq <= kMaxGridX, GLV_ERR_UNSUPPORTED);
+  const int eb = elem_bytes(dt);
+  const int epc = 16 / eb;
+  const int64_t dpad = ((int64_t)d + epc - 1) / epc * epc;
+  GLV_CHECK((size_t)C * (dpad + 4) * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
+  const int64_t bytes = (int64_t)d * eb;
+  const int nch = (int)((bytes + 15) / 16);
+  GLV_CHECK(nch <= 32 * 8, GLV_ERR_UNSUPPORTED);
+  ScoreArgs a;
+  a.Qp = Qp;
+  a.C = C;
+  a.d = d;
+  a.qstride = 0;
+  a.Xred = static_cast<const uint8_t*>(Xred);
+  a.row_stride = row_stride;
+  a.scales = scales;
+  a.tags = tags;
+  a.N = N;
+  a.off = cand_off;
+  a.ids = cand_ids;
+  a.scores = scores;
+  a.d_status = d_status;
+  a.nch = nch;
+  a.tail = (int)(bytes - (int64_t)(nch - 1) * 16);
+  a.splits = 1;
+  GLV_LAUNCH(launch_score(a, dt, nq, num_sms(), (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_topk(const float* scores, const int64_t* cand_off, const int32_t* cand_ids,
+                    int64_t nq, int32_t kappa, float* out_s, int32_t* out_id, void* stream) {
+  GLV_CHECK(nq >= 0 && kappa >= 1 && kappa <= GLV_MAX_KAPPA, GLV_ERR_INVALID_ARG);
+  if (nq == 0) return GLV_OK;
+  GLV_CHECK(scores && cand_off && cand_ids && out_s && out_id, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(nq <= kMaxGridX, GLV_ERR_UNSUPPORTED);
+  GLV_LAUNCH(launch_topk(scores, cand_off, cand_ids, nq, kappa, out_s, out_id,
+                         (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_rerank(const float* X, int64_t N, int32_t D, const float* Q, int64_t nq,
+                      const int32_t* surv_id, int32_t kappa, int32_t k, float* out_s,
+                      int32_t* out_id, int32_t* d_status, void* stream) {
+  GLV_CHECK(N >= 0 && D >= 1 && nq >= 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(kappa >= 1 && kappa <= GLV_MAX_KAPPA && k >= 1 && k <= kappa, GLV_ERR_INVALID_ARG);
+  if (nq == 0) return GLV_OK;
+  GLV_CHECK(Q && surv_id && out_s && out_id && (X || N == 0), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(nq <= kMaxGridX, GLV_ERR_UNSUPPORTED);
+  GLV_CHECK(rerank_smem_bytes(D, kappa) <= kSmemLimit, GLV_ERR_UNSUPPORTED);
+  RerankArgs a;
+  a.X = X;
+  a.N = N;
+  a.D = D;
+  a.Q = Q;
+  a.surv = surv_id;
+  a.kappa = kappa;
+  a.k = k;
+  a.out_s = out_s;
+  a.out_id = out_id;
+  a.d_status = d_status;
+  const bool vec = (D % 4 == 0) && aligned(X, 16) && aligned(Q, 16);
+  GLV_LAUNCH(launch_rerank(a, nq, vec, (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+}  // extern "C"

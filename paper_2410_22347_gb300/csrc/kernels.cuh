@@ -1,0 +1,52 @@
+// kernels.cuh -- argument blocks and launchers of the libglv kernels (host-side view).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace glv {
+
+struct ScoreArgs {
+  const float* Qp;
+  int C, d, qstride;  // qstride: floats per cluster row in shared memory (set by the launcher)
+  const uint8_t* Xred;
+  int64_t row_stride;
+  const float* scales;
+  const uint16_t* tags;
+  int64_t N;
+  const int64_t* off;
+  const int32_t* ids;
+  float* scores;
+  int32_t* d_status;
+  int nch;     // 16-byte chunks per row that hold data
+  int tail;    // bytes of data in the last chunk (16 = full)
+  int splits;  // CTAs per query (set by the launcher)
+};
+
+struct RerankArgs {
+  const float* X;
+  int64_t N;
+  int D;
+  const float* Q;
+  const int32_t* surv;
+  int kappa, k;
+  float* out_s;
+  int32_t* out_id;
+  int32_t* d_status;
+};
+
+cudaError_t launch_score(const ScoreArgs& a, int dt, int64_t nq, int num_sms, cudaStream_t st);
+cudaError_t launch_topk(const float* scores, const int64_t* off, const int32_t* ids, int64_t nq,
+                        int kappa, float* out_s, int32_t* out_id, cudaStream_t st);
+cudaError_t launch_rerank(const RerankArgs& a, int64_t nq, bool vec, cudaStream_t st);
+size_t rerank_smem_bytes(int D, int kappa);
+cudaError_t launch_project_simt(const float* Q, int64_t nq, int D, const float* A, int64_t Mcols,
+                                float* Qp, cudaStream_t st);
+size_t build_ws_bytes(int64_t N, int C);
+cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags, const float* B,
+                         int C, int d, int dt, void* Xred, int64_t row_stride, float* scales,
+                         void* workspace, int32_t* d_status, cudaStream_t st);
+cudaError_t launch_tags(const float* X, int64_t N, int D, const float* mu, int C, uint16_t* tags,
+                        int num_sms, cudaStream_t st);
+
+}  // namespace glv

@@ -1,0 +1,202 @@
+"""Thin Python binding of libglv (the C ABI in include/glv.h).
+
+Argument marshalling only: every step of the search path runs in the library's CUDA
+kernels.  Functions carry the C names and take torch CUDA tensors (for their device
+memory) plus the current torch CUDA stream; each checks shapes/dtypes, passes raw
+pointers, and raises ``GlvError`` on a non-OK status.  Importing this module loads
+``libglv.so`` and fails loudly if it is missing or broken: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build_lib
+
+GLV_OK, GLV_ERR_INVALID_ARG, GLV_ERR_BAD_ID, GLV_ERR_UNSUPPORTED, GLV_ERR_CUDA, GLV_ERR_TIMEOUT = range(6)
+GLV_F32, GLV_BF16, GLV_FP8_E4M3 = 0, 1, 2
+GLV_MAX_KAPPA = 1024
+DTYPES = {"f32": GLV_F32, "bf16": GLV_BF16, "fp8": GLV_FP8_E4M3}
+
+LIB_PATH = build_lib.LIB
+
+
+class GlvError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn} failed: {status_string(status)} (status {status})")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libglv.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python -m paper_2410_22347_gb300.build_lib")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+    sig = {
+        "glv_abi_version": (i32, []),
+        "glv_status_string": (ctypes.c_char_p, [i32]),
+        "glv_min_row_stride": (i64, [i32, i32]),
+        "glv_assign_tags": (i32, [P, i64, i32, P, i32, P, P]),
+        "glv_build_reduced_workspace_size": (sz, [i64, i32]),
+        "glv_build_reduced": (i32, [P, i64, i32, P, P, i32, i32, i32, P, i64, P, P, P, P]),
+        "glv_project_queries": (i32, [P, i64, i32, P, i32, i32, i32, P, P]),
+        "glv_score_candidates": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P]),
+        "glv_topk": (i32, [P, P, P, i64, i32, P, P, P]),
+        "glv_rerank": (i32, [P, i64, i32, P, i64, P, i32, i32, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return _lib.glv_status_string(int(s)).decode()
+
+
+def abi_version() -> int:
+    return int(_lib.glv_abi_version())
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, name: str, ndim: int | None = None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dims")
+
+
+def _check(fn: str, st: int):
+    if st != GLV_OK:
+        raise GlvError(fn, st)
+
+
+def min_row_stride(d: int, dt: int) -> int:
+    return int(_lib.glv_min_row_stride(int(d), int(dt)))
+
+
+def elem_bytes(dt: int) -> int:
+    return {GLV_F32: 4, GLV_BF16: 2, GLV_FP8_E4M3: 1}[dt]
+
+
+# ---------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------------------
+
+def glv_assign_tags(X: torch.Tensor, mu: torch.Tensor, tags: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    _need(X, torch.float32, "X", 2)
+    _need(mu, torch.float32, "mu", 2)
+    N, D = X.shape
+    if tags is None:
+        tags = torch.empty(N, dtype=torch.uint16, device=X.device)
+    _need(tags, torch.uint16, "tags", 1)
+    _check("glv_assign_tags", _lib.glv_assign_tags(_ptr(X), N, D, _ptr(mu), mu.shape[0], _ptr(tags),
+                                                   _stream(stream)))
+    return tags
+
+
+def glv_build_reduced(X, tags, B, dt: int, Xred=None, row_stride: int | None = None, scales=None,
+                      workspace=None, d_status=None, stream=None):
+    """Returns (Xred uint8 [N, row_stride], scales or None)."""
+    _need(X, torch.float32, "X", 2)
+    _need(tags, torch.uint16, "tags", 1)
+    _need(B, torch.float32, "B", 3)
+    N, D = X.shape
+    C, d, _ = B.shape
+    if row_stride is None:
+        row_stride = min_row_stride(d, dt)
+    if Xred is None:
+        Xred = torch.empty(N, row_stride, dtype=torch.uint8, device=X.device)
+    if dt == GLV_FP8_E4M3 and scales is None:
+        scales = torch.empty(N, dtype=torch.float32, device=X.device)
+    if workspace is None:
+        ws = int(_lib.glv_build_reduced_workspace_size(N, C))
+        workspace = torch.empty(max(ws, 1), dtype=torch.uint8, device=X.device)
+    _check("glv_build_reduced",
+           _lib.glv_build_reduced(_ptr(X), N, D, _ptr(tags), _ptr(B), C, d, dt, _ptr(Xred),
+                                  row_stride, _ptr(scales), _ptr(workspace), _ptr(d_status),
+                                  _stream(stream)))
+    return Xred, scales
+
+
+def glv_project_queries(Q, A, compute: int = GLV_F32, Qp=None, stream=None):
+    _need(Q, torch.float32, "Q", 2)
+    _need(A, torch.float32, "A", 3)
+    nq, D = Q.shape
+    C, d, _ = A.shape
+    if Qp is None:
+        Qp = torch.empty(nq, C, d, dtype=torch.float32, device=Q.device)
+    _check("glv_project_queries",
+           _lib.glv_project_queries(_ptr(Q), nq, D, _ptr(A), C, d, compute, _ptr(Qp), _stream(stream)))
+    return Qp
+
+
+def glv_score_candidates(Qp, Xred, row_stride: int, scales, dt: int, tags, off, ids, scores=None,
+                         d_status=None, stream=None, d: int | None = None):
+    _need(Qp, torch.float32, "Qp", 3)
+    _need(tags, torch.uint16, "tags", 1)
+    _need(off, torch.int64, "cand_off", 1)
+    _need(ids, torch.int32, "cand_ids", 1)
+    nq, C, dq = Qp.shape
+    d = dq if d is None else d
+    N = tags.shape[0]
+    if scores is None:
+        scores = torch.empty(ids.shape[0], dtype=torch.float32, device=Qp.device)
+    _check("glv_score_candidates",
+           _lib.glv_score_candidates(_ptr(Qp), nq, C, d, _ptr(Xred), row_stride, _ptr(scales), dt,
+                                     _ptr(tags), N, _ptr(off), _ptr(ids), _ptr(scores),
+                                     _ptr(d_status), _stream(stream)))
+    return scores
+
+
+def glv_topk(scores, off, ids, kappa: int, out_s=None, out_id=None, stream=None):
+    _need(scores, torch.float32, "scores", 1)
+    _need(off, torch.int64, "cand_off", 1)
+    _need(ids, torch.int32, "cand_ids", 1)
+    nq = off.shape[0] - 1
+    if out_s is None:
+        out_s = torch.empty(nq, kappa, dtype=torch.float32, device=scores.device)
+    if out_id is None:
+        out_id = torch.empty(nq, kappa, dtype=torch.int32, device=scores.device)
+    _check("glv_topk", _lib.glv_topk(_ptr(scores), _ptr(off), _ptr(ids), nq, kappa, _ptr(out_s),
+                                     _ptr(out_id), _stream(stream)))
+    return out_s, out_id
+
+
+def glv_rerank(X, Q, surv_id, k: int, out_s=None, out_id=None, d_status=None, stream=None):
+    _need(X, torch.float32, "X", 2)
+    _need(Q, torch.float32, "Q", 2)
+    _need(surv_id, torch.int32, "surv_id", 2)
+    N, D = X.shape
+    nq, kappa = surv_id.shape
+    if out_s is None:
+        out_s = torch.empty(nq, k, dtype=torch.float32, device=Q.device)
+    if out_id is None:
+        out_id = torch.empty(nq, k, dtype=torch.int32, device=Q.device)
+    _check("glv_rerank", _lib.glv_rerank(_ptr(X), N, D, _ptr(Q), nq, _ptr(surv_id), kappa, k,
+                                         _ptr(out_s), _ptr(out_id), _ptr(d_status), _stream(stream)))
+    return out_s, out_id

@@ -1,0 +1,392 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle on the same seeded inputs.
+
+Sizes here finish in seconds on the oracle yet span many tiles, several CTAs per query and
+ragged tails (odd d, lists of length 0, 1, < kappa, > the top-k key cache).  Tolerances:
+FP32 results within 1e-5 of the oracle relative to max(|s|, ||q_c|| ||x||); integer work
+(top-k ids, quantised codes) bit-exact, except where floating point decides between two
+valid answers, which is then checked for validity (see oracle/compare.py).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle.compare import scores_close, search_equivalent, topk_equivalent
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TIE = 1e-6
+
+
+@pytest.fixture(scope="module")
+def glv():
+    from paper_2410_22347_gb300 import build_lib
+    build_lib.build()
+    from paper_2410_22347_gb300 import glv as g
+    return g
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def _rng(s):
+    return np.random.default_rng(s)
+
+
+def _unit(rng, n, D):
+    x = rng.standard_normal((n, D))
+    return (x / np.linalg.norm(x, axis=1, keepdims=True)).astype(np.float32)
+
+
+def _csr(lists):
+    off = np.zeros(len(lists) + 1, np.int64)
+    off[1:] = np.cumsum([len(l) for l in lists])
+    ids = np.concatenate([np.asarray(l, np.int32) for l in lists]) if len(lists) else np.zeros(0, np.int32)
+    return off, ids.astype(np.int32)
+
+
+def _t(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to(dev()) if dtype is None else t.to(dev(), dtype)
+
+
+def _status():
+    return torch.zeros(1, dtype=torch.int32, device=dev())
+
+
+def _ragged_lists(rng, nq, N, lens):
+    return [rng.permutation(N)[:L] for L in lens]
+
+
+def _problem(seed, N=3000, D=96, d=27, C=5, nq=23, orth=True):
+    rng = _rng(seed)
+    X = _unit(rng, N, D)
+    Q = _unit(rng, nq, D)
+    mu = _unit(rng, C, D)
+    if orth:
+        A = np.stack([np.linalg.qr(rng.standard_normal((D, d)))[0].T for _ in range(C)]).astype(np.float32)
+        B = A.copy()
+    else:
+        A = (rng.standard_normal((C, d, D)) / np.sqrt(D)).astype(np.float32)
+        B = (rng.standard_normal((C, d, D)) / np.sqrt(D)).astype(np.float32)
+    tags = oracle.assign_tags(X, mu)
+    return rng, X, Q, mu, A, B, tags
+
+
+# ---------------------------------------------------------------------------------------
+# Eq. (cluster_tag)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,D,C", [(5000, 96, 7), (1000, 768, 32), (777, 33, 1), (300, 1024, 40)])
+def test_assign_tags(glv, N, D, C):
+    rng = _rng(N + D + C)
+    X = _unit(rng, N, D)
+    mu = _unit(rng, C, D)
+    if C > 3:
+        mu[3] = mu[1]  # exact ties: the lower index must win
+    ref, margin = oracle.assign_tags(X, mu, return_margin=True)
+    got = glv.glv_assign_tags(_t(X), _t(mu)).cpu().numpy()
+    sure = margin > 1e-5
+    np.testing.assert_array_equal(got[sure], ref[sure])
+    # near-ties: the GPU's choice must be (within tolerance) a maximiser
+    ip = X.astype(np.float64) @ mu.astype(np.float64).T
+    best = ip.max(axis=1)
+    assert np.all(best - ip[np.arange(N), got] <= 1e-5)
+    if C > 3:
+        assert not np.any(got == 3)
+
+
+# ---------------------------------------------------------------------------------------
+# Eq. (X_low): reduced store in FP32 / BF16 / FP8
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D,d,C,orth", [(96, 27, 5, True), (768, 160, 32, True), (64, 64, 3, False),
+                                       (100, 1, 2, False), (512, 130, 9, True)])
+def test_build_reduced_f32(glv, D, d, C, orth):
+    rng, X, Q, mu, A, B, tags = _problem(D * 7 + d, N=2500, D=D, d=d, C=C, orth=orth)
+    tags[::97] = C - 1  # make sure the last cluster is populated
+    Xr = oracle.build_reduced(X, tags, B)
+    st = _status()
+    Xred, _ = glv.glv_build_reduced(_t(X), _t(tags), _t(B), glv.GLV_F32, d_status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    rs = glv.min_row_stride(d, glv.GLV_F32)
+    raw = Xred.cpu().numpy()
+    got = raw.view(np.float32).reshape(len(X), rs // 4)
+    np.testing.assert_array_equal(got[:, d:], 0)  # padding zeroed
+    scale = np.linalg.norm(B, axis=2)[tags] * np.linalg.norm(X, axis=1)[:, None]
+    ok, worst, bad = scores_close(got[:, :d], Xr, scale, TOL)
+    assert ok, f"worst {worst}, bad at {bad[:5]}"
+
+
+def _adjacent_or_equal_codes_valid(got_codes, ref_codes, got_dec, ref_dec, exact, tol_abs, signbit):
+    """Codes may differ only by one step of the same sign, and only where the exact value
+    sits (within the FP32 error tol_abs) on the rounding midpoint between the two decoded
+    neighbours."""
+    g = got_codes.astype(np.int64)
+    r = ref_codes.astype(np.int64)
+    diff = (got_dec != ref_dec)
+    one_step = ((g & signbit) == (r & signbit)) & (np.abs((g & ~signbit) - (r & ~signbit)) == 1)
+    mid = 0.5 * (got_dec + ref_dec)
+    ok = np.all(one_step[diff]) and np.all(np.abs(exact[diff] - mid[diff]) <= tol_abs[diff])
+    return ok, int(diff.sum())
+
+
+@pytest.mark.parametrize("D,d,C", [(96, 27, 5), (768, 160, 32), (512, 128, 64)])
+def test_build_reduced_bf16(glv, D, d, C):
+    rng, X, Q, mu, A, B, tags = _problem(D + d + 1, N=3000, D=D, d=d, C=C)
+    Xr = oracle.build_reduced(X, tags, B)
+    ref_codes = oracle.bf16_encode(Xr.astype(np.float32))
+    Xred, _ = glv.glv_build_reduced(_t(X), _t(tags), _t(B), glv.GLV_BF16)
+    rs = glv.min_row_stride(d, glv.GLV_BF16)
+    got_codes = Xred.cpu().numpy().view(np.uint16).reshape(len(X), rs // 2)
+    np.testing.assert_array_equal(got_codes[:, d:], 0)
+    got_codes = got_codes[:, :d]
+    scale = np.linalg.norm(B, axis=2)[tags] * np.linalg.norm(X, axis=1)[:, None]
+    ok, ndiff = _adjacent_or_equal_codes_valid(got_codes, ref_codes, oracle.bf16_decode(got_codes),
+                                               oracle.bf16_decode(ref_codes), Xr, 2e-6 * scale, 0x8000)
+    assert ok and ndiff <= max(3, Xr.size // 1000)
+
+
+@pytest.mark.parametrize("D,d,C", [(96, 27, 5), (512, 128, 64), (768, 160, 32), (64, 16, 2)])
+def test_build_reduced_fp8(glv, D, d, C):
+    rng, X, Q, mu, A, B, tags = _problem(D + d + 2, N=3000, D=D, d=d, C=C)
+    X[11] = 0.0  # an all-zero row: scale 0, codes 0
+    Xr = oracle.build_reduced(X, tags, B)
+    ref_codes, ref_scales = oracle.quantize_fp8_rows(Xr.astype(np.float32))
+    Xred, scales = glv.glv_build_reduced(_t(X), _t(tags), _t(B), glv.GLV_FP8_E4M3)
+    rs = glv.min_row_stride(d, glv.GLV_FP8_E4M3)
+    got_codes = Xred.cpu().numpy().reshape(len(X), rs)
+    np.testing.assert_array_equal(got_codes[:, d:], 0)
+    got_codes = got_codes[:, :d]
+    got_scales = scales.cpu().numpy()
+    assert got_scales[11] == 0 and np.all(got_codes[11] == 0)
+    rowscale = np.linalg.norm(B, axis=2).max(axis=1)[tags] * np.linalg.norm(X, axis=1)
+    assert np.all(np.abs(got_scales - ref_scales) <= TOL * rowscale / 448 + 1e-30)
+    # compare in units of the scale: y = x / s
+    s64 = np.where(ref_scales > 0, ref_scales, 1).astype(np.float64)[:, None]
+    gd = oracle.e4m3_decode(got_codes)
+    rd = oracle.e4m3_decode(ref_codes)
+    y = Xr / s64
+    tol = 2e-6 * (rowscale[:, None] / s64) + np.abs(y) * 1e-6
+    ok, ndiff = _adjacent_or_equal_codes_valid(got_codes, ref_codes, gd, rd, y,
+                                               np.broadcast_to(tol, y.shape), 0x80)
+    assert ok and ndiff <= max(3, Xr.size // 1000)
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 4 preprocess: projection GEMM
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nq,D,d,C,orth", [(23, 96, 27, 5, True), (300, 768, 160, 32, True),
+                                          (129, 130, 33, 3, False), (1, 7, 3, 2, False),
+                                          (257, 512, 128, 8, True)])
+def test_project_queries_f32(glv, nq, D, d, C, orth):
+    rng, X, Q, mu, A, B, tags = _problem(nq + D, N=10, D=D, d=d, C=C, nq=nq, orth=orth)
+    ref = oracle.project(Q, A)
+    got = glv.glv_project_queries(_t(Q), _t(A)).cpu().numpy()
+    scale = np.linalg.norm(A, axis=2)[None] * np.linalg.norm(Q, axis=1)[:, None, None]
+    ok, worst, bad = scores_close(got, ref, scale, TOL)
+    assert ok, f"worst {worst}"
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 4 inner-product: gather-score, each store type, fed the oracle's own store
+# ---------------------------------------------------------------------------------------
+
+def _score_case(glv, dt, seed, d, C, lens, N=2000, D=64, bad_ids=False):
+    rng, X, Q, mu, A, B, tags = _problem(seed, N=N, D=D, d=d, C=C, nq=len(lens))
+    Xr = oracle.build_reduced(X, tags, B)
+    Qp64 = oracle.project(Q, A)
+    Qp32 = Qp64.astype(np.float32)
+    lists = _ragged_lists(rng, len(lens), N, lens)
+    if bad_ids:
+        lists[0] = np.concatenate([lists[0], [N, -3, 2 ** 31 - 1]])
+    off, ids = _csr(lists)
+    rs = glv.min_row_stride(d, dt) + (16 if seed % 2 else 0)  # also a wider-than-needed stride
+    store = np.full((N, rs), 0xAB, np.uint8)  # garbage padding: the kernel must mask it
+    scales = None
+    if dt == glv.GLV_F32:
+        x32 = Xr.astype(np.float32)
+        store[:, :4 * d] = x32.view(np.uint8).reshape(N, 4 * d)
+        xr_used = x32.astype(np.float64)
+    elif dt == glv.GLV_BF16:
+        c = oracle.bf16_encode(Xr.astype(np.float32))
+        store[:, :2 * d] = c.view(np.uint8).reshape(N, 2 * d)
+        xr_used = oracle.bf16_decode(c)
+    else:
+        c, scales = oracle.quantize_fp8_rows(Xr.astype(np.float32))
+        store[:, :d] = c
+        xr_used = oracle.dequantize_fp8_rows(c, scales)
+    ref, bad = oracle.score(Qp32.astype(np.float64), xr_used, tags, off, ids)
+    st = _status()
+    got = glv.glv_score_candidates(_t(Qp32), _t(store), rs, None if scales is None else _t(scales), dt,
+                                   _t(tags), _t(off), _t(ids), d_status=st).cpu().numpy()
+    torch.cuda.synchronize()
+    assert (st.item() == glv.GLV_ERR_BAD_ID) == bad_ids == bad
+    qn = np.linalg.norm(Qp32.astype(np.float64), axis=2)
+    xn = np.linalg.norm(xr_used, axis=1)
+    cand_j = np.repeat(np.arange(len(lens)), np.diff(off))
+    valid = (ids >= 0) & (ids < N)
+    scale = np.zeros(len(ids))
+    scale[valid] = qn[cand_j[valid], tags[ids[valid]]] * xn[ids[valid]]
+    ok, worst, badpos = scores_close(got, ref, scale, TOL)
+    assert ok, f"worst {worst} at {badpos[:5]}"
+    assert np.all(np.isneginf(got[~valid]))
+
+
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("d", [1, 27, 128, 160, 192])
+def test_score_candidates(glv, dt_name, d):
+    dt = glv.DTYPES[dt_name]
+    lens = [0, 1, 5, 64, 333, 1000, 2000, 7, 0, 1999]
+    _score_case(glv, dt, 100 + d, d, 6, lens, D=max(d, 64))
+
+
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
+def test_score_candidates_wide_rows_and_many_clusters(glv, dt_name):
+    # d large enough for the 32-lane path; C large for the shared-memory stage
+    dt = glv.DTYPES[dt_name]
+    _score_case(glv, dt, 7, 400, 3, [300, 50, 1], N=500, D=512)
+    _score_case(glv, dt, 8, 24, 300, [1500, 20], N=1600, D=48)
+
+
+def test_score_candidates_bad_ids_flagged(glv):
+    _score_case(glv, glv.GLV_F32, 5, 32, 4, [20, 3], bad_ids=True)
+
+
+def test_score_candidates_exhaustive_few_queries(glv):
+    # few queries with long lists: exercises the split of one query over many CTAs
+    _score_case(glv, glv.GLV_BF16, 9, 128, 8, [2000, 2000, 1500], N=2000, D=128)
+
+
+# ---------------------------------------------------------------------------------------
+# top-kappa: bit-exact against the oracle on the same FP32 scores
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kappa", [1, 10, 100, 257, 1024])
+def test_topk_exact(glv, kappa):
+    rng = _rng(kappa)
+    lens = [0, 1, kappa - 1 if kappa > 1 else 0, kappa, kappa + 1, 3000, 9000, 20000, 50]
+    lists = [rng.permutation(100000)[:L] for L in lens]
+    off, ids = _csr(lists)
+    s = rng.standard_normal(len(ids)).astype(np.float32)
+    # planted ties (quantised scores), repeated values, NaN and -inf
+    s[::3] = np.round(s[::3], 1)
+    s[5::101] = np.nan
+    s[7::211] = -np.inf
+    s[off[6]:off[6] + 5000] = 3.0  # a huge tie group straddling the kappa boundary
+    ref_s, ref_id = oracle.topk(s.astype(np.float64), off, ids, kappa)
+    gs, gi = glv.glv_topk(_t(s), _t(off), _t(ids), kappa)
+    gs, gi = gs.cpu().numpy(), gi.cpu().numpy()
+    np.testing.assert_array_equal(gi, ref_id)
+    np.testing.assert_array_equal(gs.astype(np.float64), ref_s)
+
+
+def test_topk_all_equal_scores(glv):
+    rng = _rng(3)
+    off, ids = _csr([rng.permutation(50000)[:12000], rng.permutation(50000)[:300]])
+    s = np.ones(len(ids), np.float32)
+    ref_s, ref_id = oracle.topk(s.astype(np.float64), off, ids, 100)
+    gs, gi = glv.glv_topk(_t(s), _t(off), _t(ids), 100)
+    np.testing.assert_array_equal(gi.cpu().numpy(), ref_id)
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 1 post-processing: exact re-rank
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D,kappa,k", [(768, 100, 10), (512, 200, 10), (97, 33, 7), (1500, 5, 5),
+                                       (64, 1024, 10), (8, 1, 1)])
+def test_rerank(glv, D, kappa, k):
+    rng = _rng(D + kappa)
+    N, nq = 4000, 19
+    X = _unit(rng, N, D)
+    Q = _unit(rng, nq, D)
+    surv = np.array([rng.permutation(N)[:kappa] for _ in range(nq)], np.int32)
+    surv[0, kappa // 2:] = -1            # partially empty
+    surv[1, :] = -1                      # fully empty
+    ref_s, ref_id, _ = oracle.rerank(X, Q, surv, k)
+    st = _status()
+    gs, gi = glv.glv_rerank(_t(X), _t(Q), _t(surv), k, d_status=st)
+    gs, gi = gs.cpu().numpy(), gi.cpu().numpy()
+    assert st.item() == 0
+    ip = Q.astype(np.float64) @ X.astype(np.float64).T
+    for j in range(nq):
+        ok, why = topk_equivalent(gi[j], ref_id[j], ref_s[j], lambda i: ip[j, i], TIE)
+        assert ok, f"query {j}: {why}"
+        v = gi[j] >= 0
+        assert np.all(np.abs(gs[j][v] - ip[j, gi[j][v]]) <= TOL)
+    assert np.all(gi[1] == -1) and np.all(np.isneginf(gs[1]))
+
+
+def test_rerank_bad_ids_flagged(glv):
+    rng = _rng(11)
+    X = _unit(rng, 50, 16)
+    Q = _unit(rng, 2, 16)
+    surv = np.array([[1, 2, 50, 3], [4, -7, 5, 6]], np.int32)
+    st = _status()
+    gs, gi = glv.glv_rerank(_t(X), _t(Q), _t(surv), 3, d_status=st)
+    torch.cuda.synchronize()
+    assert st.item() == glv.GLV_ERR_BAD_ID
+    gi = gi.cpu().numpy()
+    assert 50 not in gi[0] and -7 not in gi[1]
+
+
+# ---------------------------------------------------------------------------------------
+# whole multi-step search (FP32 store): GPU pipeline vs oracle pipeline
+# ---------------------------------------------------------------------------------------
+
+def _pipeline(glv, X, Q, A, B, tags, off, ids, kappa, k, dt):
+    st = _status()
+    Xt, Qt, tt = _t(X), _t(Q), _t(tags)
+    Xred, scales = glv.glv_build_reduced(Xt, tt, _t(B), dt, d_status=st)
+    Qp = glv.glv_project_queries(Qt, _t(A))
+    rs = glv.min_row_stride(A.shape[1], dt)
+    sc = glv.glv_score_candidates(Qp, Xred, rs, scales, dt, tt, _t(off), _t(ids), d_status=st)
+    ts, ti = glv.glv_topk(sc, _t(off), _t(ids), kappa)
+    fs, fi = glv.glv_rerank(Xt, Qt, ti, k, d_status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    return fs.cpu().numpy(), fi.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_search_pipeline_f32(glv, seed):
+    from paper_2410_22347_gb300 import synth
+    w = synth.make_workload(N=20000, D=256, d=64, C=12, nq=64, K_db=16, cands=1500, kappa=100, k=10,
+                            cfg=80 + seed)
+    X, Q, mu, A, B = (t.numpy() for t in (w.X, w.Q, w.mu, w.A, w.B))
+    off, ids = w.off.numpy(), w.ids.numpy()
+    tags = oracle.assign_tags(X, mu)
+    Xr = oracle.build_reduced(X, tags, B)
+    ref_s, ref_id = oracle.search(X, Xr, tags, A, Q, off, ids, w.kappa, w.k)
+    red, _ = oracle.score(oracle.project(Q, A), Xr, tags, off, ids)
+    kap, _ = oracle.topk(red, off, ids, w.kappa)
+    fs, fi = _pipeline(glv, X, Q, A, B, tags, off, ids, w.kappa, w.k, glv.GLV_F32)
+    for j in range(len(Q)):
+        lst = ids[off[j]:off[j + 1]]
+        rd = dict(zip(lst.tolist(), red[off[j]:off[j + 1]].tolist()))
+        ok, why = search_equivalent(fi[j], ref_id[j], ref_s[j],
+                                    lambda i: float(Q[j].astype(np.float64) @ X[i].astype(np.float64)),
+                                    lambda i: rd[i], kap[j, -1], TIE, TIE)
+        assert ok, f"query {j}: {why}"
+    assert oracle.recall(fi, ref_id) >= 0.99
+
+
+@pytest.mark.parametrize("dt_name", ["bf16", "fp8"])
+def test_search_pipeline_low_precision_recall(glv, dt_name):
+    """Low-precision stores: the final top-10 (after the exact FP32 re-rank) agrees with the
+    FP64 oracle pipeline at 10-recall@10 >= 0.9."""
+    from paper_2410_22347_gb300 import synth
+    w = synth.make_workload(N=20000, D=256, d=64, C=12, nq=64, K_db=16, cands=1500, kappa=100, k=10,
+                            cfg=85)
+    X, Q, mu, A, B = (t.numpy() for t in (w.X, w.Q, w.mu, w.A, w.B))
+    off, ids = w.off.numpy(), w.ids.numpy()
+    tags = oracle.assign_tags(X, mu)
+    Xr = oracle.build_reduced(X, tags, B)
+    ref_s, ref_id = oracle.search(X, Xr, tags, A, Q, off, ids, w.kappa, w.k)
+    fs, fi = _pipeline(glv, X, Q, A, B, tags, off, ids, w.kappa, w.k, glv.DTYPES[dt_name])
+    assert oracle.recall(fi, ref_id) >= 0.9
