@@ -130,8 +130,10 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(const float* __restr
       const uint32_t k = key_of(p);
       if (k > kstar) {
         const uint32_t slot = atomicAdd(&S.count, 1u);
-        S.sel_key[slot] = k;
-        S.sel_id[slot] = ij[p];
+        if (slot < (uint32_t)kappa) {
+          S.sel_key[slot] = k;
+          S.sel_id[slot] = ij[p];
+        }
       } else if (k == kstar) {
         atomicAdd(&S.n_eq, 1u);
       }
