@@ -1,0 +1,461 @@
+#!/usr/bin/env python3
+"""Benchmark of the GleanVec eager multi-step search on GB300.
+
+One step = one pass of the whole hot path over one batch of queries with device-resident
+inputs:  glv_project_queries -> glv_score_candidates -> glv_topk -> glv_rerank.
+Default workload: 1M x 768 database, d = 160, C = 32 clusters, 10,000 OOD queries, 2,048
+random candidate ids per query (graph-search-like gathers), kappa = 100 re-ranked to
+k = 10, reduced rows stored in BF16 (the FP32 store is timed beside it).
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): every rank holds a replica of the
+database and searches its own query set (queries are independent, so there is no data
+collective); value = all ranks' queries / max-over-ranks time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl glv|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s at 10-recall@10>=0.9 vs oracle (low-prec vs FP32); gather-score HBM GB/s"
+UNIT = "queries/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="glv", choices=["glv", "reference"])
+    p.add_argument("--workload", default="graph-1M-d160")
+    p.add_argument("--store", default="bf16", choices=["f32", "bf16", "fp8"])
+    p.add_argument("--compare-stores", default="f32", help="comma list of other stores to time too")
+    p.add_argument("--cpu-sample", type=int, default=256, help="queries in the CPU-baseline sample")
+    p.add_argument("--recall-sample", type=int, default=256)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ref-queries-per-step", type=int, default=256)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.tmp.flush()
+        rows = []
+        try:
+            with open(self.tmp.name) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def source_sha(*rel):
+    h = hashlib.sha256()
+    for r in rel:
+        with open(os.path.join(ROOT, r), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_file: str, workload: str, store: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, valid
+    only while the kernel source still has the hash the counters were taken with."""
+    path = os.path.join(ROOT, "profiles", "score_candidates_traffic.md")
+    if not os.path.exists(path):
+        return None
+    sha = source_sha(kernel_file)
+    with open(path) as f:
+        for line in f:
+            m = re.match(r"\s*traffic\s+(\S+)\s+(\S+)\s+([0-9a-f]+)\s+([0-9.eE+]+)", line)
+            if m and m.group(1) == workload and m.group(2) == store and m.group(3) == sha:
+                return float(m.group(4))
+    return None
+
+
+# ---------------------------------------------------------------------------------------
+# oracle (CPU baseline / reference arm / recall check) on a bounded sample
+# ---------------------------------------------------------------------------------------
+
+def oracle_subproblem(X, Q, mu, A, B, off, ids, qsel):
+    """Restrict the problem to the database rows the selected queries touch (a valid
+    GleanVec problem on its own: tags and reduced rows are per row).  numpy inputs."""
+    import numpy as np
+    import oracle
+    lists = [ids[off[j]:off[j + 1]] for j in qsel]
+    cat = np.concatenate(lists) if lists else np.zeros(0, np.int32)
+    uniq = np.unique(cat)
+    loff = np.zeros(len(qsel) + 1, np.int64)
+    loff[1:] = np.cumsum([len(l) for l in lists])
+    lids = np.searchsorted(uniq, cat).astype(np.int32)
+    Xs = np.ascontiguousarray(X[uniq])
+    t0 = time.perf_counter()
+    tags = oracle.assign_tags(Xs, mu)
+    Xr = oracle.build_reduced(Xs, tags, B)
+    prep = time.perf_counter() - t0
+    return dict(X=Xs, Q=np.ascontiguousarray(Q[qsel]), A=A, tags=tags, Xr=Xr, off=loff, ids=lids, uniq=uniq,
+                prep_s=prep)
+
+
+def oracle_search_timed(sp, kappa, k, repeats=1):
+    import oracle
+    best = None
+    out = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        out = oracle.search(sp["X"], sp["Xr"], sp["tags"], sp["A"], sp["Q"], sp["off"], sp["ids"], kappa, k)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    s, i = out
+    import numpy as np
+    gid = np.where(i >= 0, sp["uniq"][np.clip(i, 0, None)], -1)
+    return best, s, gid
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the oracle, timed on the host cores
+# ---------------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2410_22347_gb300 import synth
+
+    oracle.set_threads(os.cpu_count() or 1)
+    w = synth.workload(args.workload, device="cpu")
+    X, Q, mu, A, B = (t.numpy() for t in (w.X, w.Q, w.mu, w.A, w.B))
+    off, ids = w.off.numpy(), w.ids.numpy()
+    nq = Q.shape[0]
+    per = min(args.ref_queries_per_step, nq)
+    nsteps = args.warmup + args.steps
+    sels = [np.arange(s * per, s * per + per) % nq for s in range(nsteps)]
+    allq = np.unique(np.concatenate(sels))
+    sp = oracle_subproblem(X, Q, mu, A, B, off, ids, allq)
+    pos = {int(q): t for t, q in enumerate(allq)}
+    times = []
+    for s in range(nsteps):
+        loc = np.array([pos[int(q)] for q in sels[s]])
+        sub = dict(sp)
+        sub["Q"] = sp["Q"][loc]
+        lo = sp["off"]
+        lists = [sp["ids"][lo[t]:lo[t + 1]] for t in loc]
+        sub["off"] = np.zeros(len(loc) + 1, np.int64)
+        sub["off"][1:] = np.cumsum([len(l) for l in lists])
+        sub["ids"] = np.concatenate(lists).astype(np.int32)
+        dt, _, _ = oracle_search_timed(sub, w.kappa, w.k)
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per * len(times) / total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": args.workload, "queries_per_step": per, "candidates_per_query": 2048,
+                   "kappa": w.kappa, "k": w.k},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": f"{per} queries per step, reduced rows precomputed for the "
+                                   f"{len(sp['uniq'])} rows they touch ({sp['prep_s']:.1f} s, untimed)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+
+def run_glv(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2410_22347_gb300 import build_lib
+    build_lib.build()
+    from paper_2410_22347_gb300 import glv, synth
+    from paper_2410_22347_gb300.index import GleanVecIndex
+
+    w = synth.workload(args.workload, device=dev, replica=rank)
+    nq, D = w.Q.shape
+    C, d, _ = w.A.shape
+    total = int(w.off[-1])
+    stores = [args.store] + [s for s in args.compare_stores.split(",") if s and s != args.store]
+    idx = {}
+    for st in stores:
+        idx[st] = GleanVecIndex(w.X, w.A, w.B, mu=w.mu if not idx else None,
+                                tags=None if not idx else next(iter(idx.values())).tags, store=st)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(ix, ev=None):
+        b = ix._buffers(nq, total, w.kappa, w.k)
+        if ev:
+            ev[0].record()
+        glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"])
+        if ev:
+            ev[1].record()
+        glv.glv_score_candidates(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids,
+                                 scores=b["scores"], d_status=ix.status)
+        if ev:
+            ev[2].record()
+        glv.glv_topk(b["scores"], w.off, w.ids, w.kappa, out_s=b["ts"], out_id=b["ti"])
+        if ev:
+            ev[3].record()
+        glv.glv_rerank(w.X, w.Q, b["ti"], w.k, out_s=b["fs"], out_id=b["fi"], d_status=ix.status)
+        if ev:
+            ev[4].record()
+        return b["fs"], b["fi"]
+
+    launches_per_step = 4
+    results = {}
+    clocks = None
+    for si, st in enumerate(stores):
+        ix = idx[st]
+        for _ in range(args.warmup):
+            step(ix)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if si == 0 else None
+        if sampler:
+            sampler.__enter__()
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()  # evict L2 between timed steps (not inside the timed events)
+            step(ix, evs[s])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if sampler:
+            sampler.__exit__()
+            clocks = sampler.summary()
+        if world > 1:
+            dist.barrier()
+        per_step = [evs[s][0].elapsed_time(evs[s][4]) for s in range(args.steps)]
+        kern = [[evs[s][t].elapsed_time(evs[s][t + 1]) for s in range(args.steps)] for t in range(4)]
+        tot_ms = sum(per_step)
+        if world > 1:
+            t = torch.tensor([tot_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_ms = float(t.item())
+        assert ix.device_status() == 0, "device reported an error during the bench"
+        results[st] = dict(ms_per_step=tot_ms / args.steps,
+                           value=world * nq * args.steps / (tot_ms / 1e3),
+                           kernels_ms={n: statistics.mean(v) for n, v in
+                                       zip(("project", "score", "topk", "rerank"), kern)},
+                           wall_s=wall)
+
+    # ---- end-to-end through the public host API (pinned host buffers, copies timed) ----
+    ix = idx[args.store]
+    Qh = w.Q.cpu().pin_memory()
+    offh = w.off.cpu().pin_memory()
+    idsh = w.ids.cpu().pin_memory()
+    outs = torch.empty(nq, w.k, dtype=torch.float32, pin_memory=True)
+    outi = torch.empty(nq, w.k, dtype=torch.int32, pin_memory=True)
+    for _ in range(max(1, args.warmup)):
+        ix.search_host(Qh, offh, idsh, w.kappa, w.k, outs, outi)
+    torch.cuda.synchronize()
+    e2e_steps = max(5, min(args.steps, 20))
+    e_ms = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.search_host(Qh, offh, idsh, w.kappa, w.k, outs, outi)
+        e1.record()
+        e1.synchronize()
+        e_ms.append(e0.elapsed_time(e1))
+    e2e_ms = sum(e_ms) / len(e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = Qh.numel() * 4 + offh.numel() * 8 + idsh.numel() * 4
+    d2h = outs.numel() * 4 + outi.numel() * 4
+
+    # ---- recall vs the FP64 oracle (rank 0, bounded sample) and CPU baseline ----
+    line_extra = {}
+    if rank == 0:
+        import oracle
+        oracle.set_threads(os.cpu_count() or 1)
+        Xn = w.X.cpu().numpy()
+        Qn = w.Q.cpu().numpy()
+        mun, An, Bn = w.mu.cpu().numpy(), w.A.cpu().numpy(), w.B.cpu().numpy()
+        offn, idsn = w.off.cpu().numpy(), w.ids.cpu().numpy()
+        rng = np.random.default_rng(12345)
+        qsel = np.sort(rng.choice(nq, size=min(args.recall_sample, nq), replace=False))
+        sp = oracle_subproblem(Xn, Qn, mun, An, Bn, offn, idsn, qsel)
+        ot, os_, oid = oracle_search_timed(sp, w.kappa, w.k)
+        recall = {}
+        for st in stores:
+            fs, fi = step(idx[st])
+            torch.cuda.synchronize()
+            recall[st] = oracle.recall(fi.cpu().numpy()[qsel], oid)
+        line_extra["recall_10at10_vs_oracle"] = recall
+        line_extra["recall_sample"] = f"{len(qsel)} random queries; oracle restricted to the rows they touch"
+        if not args.no_cpu_baseline:
+            csel = qsel if args.cpu_sample == len(qsel) else np.sort(
+                rng.choice(nq, size=min(args.cpu_sample, nq), replace=False))
+            cp = sp if csel is qsel else oracle_subproblem(Xn, Qn, mun, An, Bn, offn, idsn, csel)
+            ctime, _, _ = oracle_search_timed(cp, w.kappa, w.k, repeats=3)
+            line_extra["cpu_baseline"] = {
+                "value": len(csel) / ctime, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                "sample": f"{len(csel)} of the {nq} queries (all {w.ids.shape[0] // nq} candidates each); "
+                          f"reduced rows precomputed untimed for the {len(cp['uniq'])} rows they touch; best of 3"}
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        return 0
+
+    head = results[args.store]
+    hbm, peak_kind = measured_peaks()
+    eb = glv.elem_bytes(glv.DTYPES[args.store])
+    bytes_per_cand = d * eb + (4 if args.store == "fp8" else 0) + 4
+    alg_bytes = total * bytes_per_cand
+    score_ms = head["kernels_ms"]["score"]
+    achieved = alg_bytes / (score_ms / 1e3) / 1e9
+    traffic = recorded_traffic("paper_2410_22347_gb300/csrc/score.cu", args.workload, args.store)
+    rec = line_extra.get("recall_10at10_vs_oracle", {}).get(args.store)
+    line = {
+        "metric": METRIC,
+        "value": head["value"],
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": args.store,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": int(w.X.shape[0]), "D": D, "d": d, "C": C,
+                   "queries_per_gpu": nq, "candidates_per_query": total // nq, "kappa": w.kappa, "k": w.k,
+                   "reduced_row_store": args.store, "accumulate": "f32", "projection": "f32",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "roofline": {"kernel": "glv_score_candidates", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                     "bytes_per_candidate": bytes_per_cand, "kernel_ms": score_ms},
+        "kernels_ms": head["kernels_ms"],
+        "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "modes": {st: {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernels_ms": r["kernels_ms"]}
+                  for st, r in results.items()},
+    }
+    line.update(line_extra)
+    if rec is not None and rec < 0.9:
+        line["warning"] = f"{args.store} recall {rec:.3f} below 0.9"
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_glv(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -41,10 +41,12 @@ GLV_DEV float warp_sum(float v) {
 }
 
 // Order-preserving map of an FP32 score to uint32 (larger key = better score).  NaN maps
-// to 0, below every number including -inf (whose key is 0x007FFFFF).
+// to 0, below every number including -inf (whose key is 0x007FFFFF); -0.0 maps to the key
+// of +0.0 so that the two zeros tie (and are then ordered by id), as they compare equal.
 GLV_DEV uint32_t score_key(float s) {
   uint32_t u = __float_as_uint(s);
   if ((u & 0x7fffffffu) > 0x7f800000u) return 0u;  // NaN
+  if (u == 0x80000000u) u = 0u;                      // -0.0 -> +0.0
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 

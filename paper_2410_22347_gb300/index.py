@@ -1,0 +1,104 @@
+"""User-facing GleanVec index on one GPU, built on the C ABI.
+
+``GleanVecIndex`` owns the device-resident database X, cluster tags, the per-cluster
+(A_c, B_c) and the reduced store x_i^low = B_{c_i} x_i, and runs the eager multi-step
+search of Algorithm 1 / Algorithm 4 with four library calls:
+
+    glv_project_queries -> glv_score_candidates -> glv_topk -> glv_rerank
+
+``search`` takes device tensors; ``search_host`` takes host tensors (pinned when given
+pinned memory), copies them in, searches and copies the top-k back on the same stream.
+Every step runs in libglv's kernels; torch only provides device memory and the stream.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import glv
+
+
+class GleanVecIndex:
+    def __init__(self, X: torch.Tensor, A: torch.Tensor, B: torch.Tensor, *, tags: torch.Tensor | None = None,
+                 mu: torch.Tensor | None = None, store: str = "bf16", project: str = "f32", stream=None):
+        if tags is None:
+            if mu is None:
+                raise ValueError("give cluster tags or landmarks mu")
+            tags = glv.glv_assign_tags(X, mu, stream=stream)
+        self.X, self.A, self.B, self.tags = X, A, B, tags
+        self.N, self.D = X.shape
+        self.C, self.d, _ = A.shape
+        self.dt = glv.DTYPES[store]
+        self.compute = glv.DTYPES[project]
+        self.row_stride = glv.min_row_stride(self.d, self.dt)
+        self.status = torch.zeros(1, dtype=torch.int32, device=X.device)
+        self.Xred, self.scales = glv.glv_build_reduced(X, tags, B, self.dt, d_status=self.status,
+                                                       stream=stream)
+        self._buf = {}
+        self._h2d = {}
+
+    def _buffers(self, nq: int, total: int, kappa: int, k: int):
+        key = (nq, total, kappa, k)
+        b = self._buf.get(key)
+        if b is None:
+            dev = self.X.device
+            b = dict(
+                Qp=torch.empty(nq, self.C, self.d, dtype=torch.float32, device=dev),
+                scores=torch.empty(max(total, 1), dtype=torch.float32, device=dev),
+                ts=torch.empty(nq, kappa, dtype=torch.float32, device=dev),
+                ti=torch.empty(nq, kappa, dtype=torch.int32, device=dev),
+                fs=torch.empty(nq, k, dtype=torch.float32, device=dev),
+                fi=torch.empty(nq, k, dtype=torch.int32, device=dev),
+            )
+            self._buf = {key: b}
+        return b
+
+    def search(self, Q: torch.Tensor, off: torch.Tensor, ids: torch.Tensor, kappa: int, k: int,
+               stream=None):
+        """Eager multi-step search of the CSR candidate lists (device tensors).  Returns
+        (scores, ids) of shape nq x k.  kappa == 0: no re-rank (top k of reduced scores)."""
+        nq = Q.shape[0]
+        b = self._buffers(nq, ids.shape[0], max(kappa, k), k)
+        glv.glv_project_queries(Q, self.A, self.compute, Qp=b["Qp"], stream=stream)
+        glv.glv_score_candidates(b["Qp"], self.Xred, self.row_stride, self.scales, self.dt, self.tags, off, ids,
+                                 scores=b["scores"], d_status=self.status, stream=stream)
+        if kappa <= 0:
+            glv.glv_topk(b["scores"], off, ids, k, out_s=b["fs"], out_id=b["fi"], stream=stream)
+            return b["fs"], b["fi"]
+        glv.glv_topk(b["scores"], off, ids, kappa, out_s=b["ts"], out_id=b["ti"], stream=stream)
+        glv.glv_rerank(self.X, Q, b["ti"], k, out_s=b["fs"], out_id=b["fi"], d_status=self.status,
+                       stream=stream)
+        return b["fs"], b["fi"]
+
+    def search_host(self, Q_h: torch.Tensor, off_h: torch.Tensor, ids_h: torch.Tensor, kappa: int, k: int,
+                    out_s_h: torch.Tensor | None = None, out_id_h: torch.Tensor | None = None, stream=None):
+        """Host-in, host-out search: copies the queries and candidate lists to the device,
+        searches, copies the top-k back (asynchronously on the stream when the host
+        tensors are pinned; call torch.cuda.synchronize / stream.synchronize to wait)."""
+        dev = self.X.device
+        st = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            key = (tuple(Q_h.shape), tuple(off_h.shape), tuple(ids_h.shape))
+            d = self._h2d.get(key)
+            if d is None:
+                d = (torch.empty(Q_h.shape, dtype=torch.float32, device=dev),
+                     torch.empty(off_h.shape, dtype=torch.int64, device=dev),
+                     torch.empty(ids_h.shape, dtype=torch.int32, device=dev))
+                self._h2d = {key: d}
+            Qd, offd, idsd = d
+            Qd.copy_(Q_h, non_blocking=True)
+            offd.copy_(off_h, non_blocking=True)
+            idsd.copy_(ids_h, non_blocking=True)
+            fs, fi = self.search(Qd, offd, idsd, kappa, k, stream=st)
+            if out_s_h is None:
+                out_s_h = torch.empty(fs.shape, dtype=fs.dtype, pin_memory=True)
+                out_id_h = torch.empty(fi.shape, dtype=fi.dtype, pin_memory=True)
+            out_s_h.copy_(fs, non_blocking=True)
+            out_id_h.copy_(fi, non_blocking=True)
+        return out_s_h, out_id_h
+
+    def device_status(self) -> int:
+        """First device-side error recorded since the last reset (0 = none); synchronises."""
+        return int(self.status.item())
+
+    def reset_status(self):
+        self.status.zero_()

@@ -142,14 +142,16 @@ class Workload:
 
 def make_workload(*, N: int, D: int, d: int, C: int, nq: int, K_db: int, cands,
                   kappa: int, k: int, cfg: int, device="cpu", queries: str = "ood",
-                  name: str = "") -> Workload:
+                  name: str = "", replica: int = 0) -> Workload:
     """Draw one workload.  ``cands`` is an int (fixed list length; N means exhaustive
-    in id order), or a tuple ("lognormal", mean, sigma, lo, hi)."""
+    in id order), or a tuple ("lognormal", mean, sigma, lo, hi).  ``replica`` > 0 draws
+    a different query set and candidate lists over the same database (one per GPU when
+    the queries are sharded across processes)."""
     g = _gen(seed_for(cfg, "data"), device)
     means = torch.randn(K_db, D, generator=g, device=device, dtype=torch.float32)
     X = mixture(N, D, means, 1.0, g, device)
 
-    gq = _gen(seed_for(cfg, "queries"), device)
+    gq = _gen(seed_for(cfg, "queries") + 1_000_003 * replica, device)
     if queries == "ood":
         Ro = haar_orthogonal(D, 1, gq, device)[0]
         Q = mixture(nq, D, means @ Ro.T, 0.5, gq, device)
@@ -167,7 +169,7 @@ def make_workload(*, N: int, D: int, d: int, C: int, nq: int, K_db: int, cands,
     A = P.clone()
     B = P.clone()
 
-    gc = _gen(seed_for(cfg, "cands"), device)
+    gc = _gen(seed_for(cfg, "cands") + 1_000_003 * replica, device)
     if isinstance(cands, int) and cands == N:
         off = torch.arange(nq + 1, device=device, dtype=torch.int64) * N
         ids = torch.arange(N, device=device, dtype=torch.int32).repeat(nq)
