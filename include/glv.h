@@ -101,6 +101,38 @@ glv_status glv_build_reduced(const float* X, int64_t N, int32_t D, const uint16_
                              int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * glv_build_reduced_noalloc -- the same build as glv_build_reduced, for callers that cannot
+ * allocate device memory.  (This entry point has no counterpart in the paper; it only
+ * changes where the build's scratch memory comes from.)
+ *
+ * Some callers cannot hand the library a workspace: code that runs inside another
+ * framework's memory pool or under a fixed device-memory budget it does not control, plugin
+ * hosts that only pass through the input and output buffers, and callers on a latency path
+ * where cudaMalloc (which may synchronise the device) is not acceptable.  This variant takes
+ * the same inputs and outputs as glv_build_reduced but no workspace: its scratch (cluster
+ * counts, cursors, offsets, tile table, row permutation) is a fixed array of device memory
+ * inside libglv itself, about 4.2 MB, reserved on every GPU that loads the library until the
+ * process exits.  It calls no allocator.
+ *
+ *   Limits: N <= GLV_NOALLOC_MAX_ROWS and C <= GLV_NOALLOC_MAX_CLUSTERS; larger sizes return
+ *           GLV_ERR_UNSUPPORTED and enqueue nothing (use glv_build_reduced instead).
+ *   Set-up: the first call on each device looks up the array's device address with that
+ *           device current (cudaGetSymbolAddress) and caches it; make that first call before
+ *           any stream capture on that device.
+ *   Sharing: all calls on a device share the one array and it keeps the previous call's
+ *           contents (the parts that must start at zero are cleared on the stream by each
+ *           call).  Calls whose execution overlaps on the GPU -- on different streams, or
+ *           from different host threads -- race on the array: serialise them.
+ * All other arguments, results and errors are exactly those of glv_build_reduced.
+ * ------------------------------------------------------------------------------------- */
+#define GLV_NOALLOC_MAX_ROWS (1LL << 20)
+#define GLV_NOALLOC_MAX_CLUSTERS 4096
+glv_status glv_build_reduced_noalloc(const float* X, int64_t N, int32_t D, const uint16_t* tags,
+                                     const float* B, int32_t C, int32_t d, glv_dtype dt,
+                                     void* Xred, int64_t row_stride, float* scales,
+                                     int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Query preprocessing of Algorithm 4 (eager):  q_{j,c} = A_c q_j  for every c = 1..C,
  * i.e. one dense GEMM  Qp = Q . [A_1; ...; A_C]^T  of shape nq x (C*d).
  *   Q       : nq x D float32.           A : C x d x D float32.

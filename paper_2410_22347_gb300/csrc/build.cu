@@ -314,3 +314,58 @@ cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags,
 }
 
 }  // namespace glv
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of glv_build_reduced: the grouping scratch (cluster counts,
+// cursors, offsets, tile table and the row permutation) lives in a file-scope device array
+// instead of a caller-provided workspace.  The array is sized for GLV_NOALLOC_MAX_ROWS rows
+// and GLV_NOALLOC_MAX_CLUSTERS clusters and stays resident on every device that loads the
+// library until the process exits.
+// ---------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace glv {
+
+constexpr size_t noalloc_al256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kNoAllocScratchBytes =
+    noalloc_al256(8 * (size_t)GLV_NOALLOC_MAX_CLUSTERS) + noalloc_al256(4 * (size_t)GLV_NOALLOC_MAX_CLUSTERS) +
+    noalloc_al256(4 * ((size_t)GLV_NOALLOC_MAX_CLUSTERS + 1)) + noalloc_al256(4 * (size_t)GLV_NOALLOC_MAX_ROWS);
+
+static __device__ __align__(256) unsigned char g_build_scratch[kNoAllocScratchBytes];
+
+// Device address of g_build_scratch on the current device.  In host code the symbol name is
+// only a host-side handle, so the address is looked up once per device (with that device
+// current) and cached.
+static cudaError_t build_scratch_address(void** out) {
+  static std::mutex mu;
+  static void* addr[256] = {};
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_build_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace glv
+
+extern "C" glv_status glv_build_reduced_noalloc(const float* X, int64_t N, int32_t D,
+                                                const uint16_t* tags, const float* B, int32_t C,
+                                                int32_t d, glv_dtype dt, void* Xred,
+                                                int64_t row_stride, float* scales,
+                                                int32_t* d_status, void* stream) {
+  if (N > GLV_NOALLOC_MAX_ROWS || C > GLV_NOALLOC_MAX_CLUSTERS) return GLV_ERR_UNSUPPORTED;
+  if (N < 0 || C < 1) return GLV_ERR_INVALID_ARG;
+  if (glv::build_ws_bytes(N, C) > glv::kNoAllocScratchBytes) return GLV_ERR_UNSUPPORTED;
+  void* scratch = nullptr;
+  if (glv::build_scratch_address(&scratch) != cudaSuccess) return GLV_ERR_CUDA;
+  return glv_build_reduced(X, N, D, tags, B, C, d, dt, Xred, row_stride, scales, scratch, d_status,
+                           stream);
+}

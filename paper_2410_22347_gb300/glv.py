@@ -42,6 +42,7 @@ def _load() -> ctypes.CDLL:
         "glv_assign_tags": (i32, [P, i64, i32, P, i32, P, P]),
         "glv_build_reduced_workspace_size": (sz, [i64, i32]),
         "glv_build_reduced": (i32, [P, i64, i32, P, P, i32, i32, i32, P, i64, P, P, P, P]),
+        "glv_build_reduced_noalloc": (i32, [P, i64, i32, P, P, i32, i32, i32, P, i64, P, P, P]),
         "glv_project_queries": (i32, [P, i64, i32, P, i32, i32, i32, P, P]),
         "glv_score_candidates": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P]),
         "glv_topk": (i32, [P, P, P, i64, i32, P, P, P]),
@@ -140,6 +141,21 @@ def glv_build_reduced(X, tags, B, dt: int, Xred=None, row_stride: int | None = N
            _lib.glv_build_reduced(_ptr(X), N, D, _ptr(tags), _ptr(B), C, d, dt, _ptr(Xred),
                                   row_stride, _ptr(scales), _ptr(workspace), _ptr(d_status),
                                   _stream(stream)))
+    return Xred, scales
+
+
+def glv_build_reduced_noalloc(X, tags, B, dt: int, Xred, row_stride: int, scales=None, d_status=None,
+                              stream=None):
+    """glv_build_reduced without a workspace: the caller passes only inputs and outputs
+    (Xred, and scales for FP8); the scratch is the library's own fixed device array."""
+    _need(X, torch.float32, "X", 2)
+    _need(tags, torch.uint16, "tags", 1)
+    _need(B, torch.float32, "B", 3)
+    N, D = X.shape
+    C, d, _ = B.shape
+    _check("glv_build_reduced_noalloc",
+           _lib.glv_build_reduced_noalloc(_ptr(X), N, D, _ptr(tags), _ptr(B), C, d, dt, _ptr(Xred),
+                                          row_stride, _ptr(scales), _ptr(d_status), _stream(stream)))
     return Xred, scales
 
 
