@@ -43,12 +43,19 @@ def parse():
     p.add_argument("--impl", default="glv", choices=["glv", "reference"])
     p.add_argument("--workload", default="graph-1M-d160")
     p.add_argument("--store", default="bf16", choices=["f32", "bf16", "fp8"])
-    p.add_argument("--compare-stores", default="f32", help="comma list of other stores to time too")
+    p.add_argument("--compare-stores", default="fp8,f32", help="comma list of other stores to time too")
     p.add_argument("--cpu-sample", type=int, default=256, help="queries in the CPU-baseline sample")
     p.add_argument("--recall-sample", type=int, default=256)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-queries-per-step", type=int, default=256)
-    return p.parse_args()
+    p.add_argument("--override", nargs="*", default=[],
+                   help="workload fields to override, e.g. nq=2000 D=256 (smaller profiling cases)")
+    a = p.parse_args()
+    a.overrides = {}
+    for kv in a.override:
+        k, v = kv.split("=", 1)
+        a.overrides[k] = int(v)
+    return a
 
 
 # ---------------------------------------------------------------------------------------
@@ -60,6 +67,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float) -> float:
+    """Max of a per-rank float over the process group (identity without one).  Used for the
+    step time: the job is as slow as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(per_rank_units: int, world: int, max_ms: float) -> float:
+    """Whole-job units per second: every rank processed per_rank_units in at most max_ms."""
+    return world * per_rank_units / (max_ms / 1e3)
 
 
 def measured_peaks():
@@ -91,6 +116,12 @@ class ClockSampler:
                  "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # wait for the first sample, so nvidia-smi's start-up is over before timing starts
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 10:
+            if os.path.getsize(self.tmp.name) > 0:
+                break
+            time.sleep(0.05)
         return self
 
     def __exit__(self, *a):
@@ -137,13 +168,17 @@ def source_sha(*rel):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_file: str, workload: str, store: str):
+KERNEL_SOURCES = ("paper_2410_22347_gb300/csrc/fused.cu", "paper_2410_22347_gb300/csrc/score_dev.cuh",
+                  "paper_2410_22347_gb300/csrc/topk_dev.cuh", "paper_2410_22347_gb300/csrc/common.cuh")
+
+
+def recorded_traffic(workload: str, store: str):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, valid
     only while the kernel source still has the hash the counters were taken with."""
-    path = os.path.join(ROOT, "profiles", "score_candidates_traffic.md")
+    path = os.path.join(ROOT, "profiles", "score_topk_traffic.md")
     if not os.path.exists(path):
         return None
-    sha = source_sha(kernel_file)
+    sha = source_sha(*KERNEL_SOURCES)
     with open(path) as f:
         for line in f:
             m = re.match(r"\s*traffic\s+(\S+)\s+(\S+)\s+([0-9a-f]+)\s+([0-9.eE+]+)", line)
@@ -205,7 +240,7 @@ def run_reference(args):
     from paper_2410_22347_gb300 import synth
 
     oracle.set_threads(os.cpu_count() or 1)
-    w = synth.workload(args.workload, device="cpu")
+    w = synth.workload(args.workload, device="cpu", **args.overrides)
     X, Q, mu, A, B = (t.numpy() for t in (w.X, w.Q, w.mu, w.A, w.B))
     off, ids = w.off.numpy(), w.ids.numpy()
     nq = Q.shape[0]
@@ -267,11 +302,11 @@ def run_glv(args):
     from paper_2410_22347_gb300 import glv, synth
     from paper_2410_22347_gb300.index import GleanVecIndex
 
-    w = synth.workload(args.workload, device=dev, replica=rank)
+    w = synth.workload(args.workload, device=dev, replica=rank, **args.overrides)
     nq, D = w.Q.shape
     C, d, _ = w.A.shape
     total = int(w.off[-1])
-    stores = [args.store] + [s for s in args.compare_stores.split(",") if s and s != args.store]
+    stores = [args.store] + [s for s in args.compare_stores.split(",") if s and s not in (args.store, "none")]
     idx = {}
     for st in stores:
         idx[st] = GleanVecIndex(w.X, w.A, w.B, mu=w.mu if not idx else None,
@@ -284,22 +319,19 @@ def run_glv(args):
         b = ix._buffers(nq, total, w.kappa, w.k)
         if ev:
             ev[0].record()
-        glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"])
+        glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"], d_status=ix.status)
         if ev:
             ev[1].record()
-        glv.glv_score_candidates(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids,
-                                 scores=b["scores"], d_status=ix.status)
+        glv.glv_score_topk(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids, w.kappa,
+                           scores_scratch=b["scores"], out_s=b["ts"], out_id=b["ti"], d_status=ix.status)
         if ev:
             ev[2].record()
-        glv.glv_topk(b["scores"], w.off, w.ids, w.kappa, out_s=b["ts"], out_id=b["ti"])
-        if ev:
-            ev[3].record()
         glv.glv_rerank(w.X, w.Q, b["ti"], w.k, out_s=b["fs"], out_id=b["fi"], d_status=ix.status)
         if ev:
-            ev[4].record()
+            ev[3].record()
         return b["fs"], b["fi"]
 
-    launches_per_step = 4
+    launches_per_step = 3 + 2  # projection: 2 operand-prep launches + GEMM; fused score+top-k; re-rank
     results = {}
     clocks = None
     for si, st in enumerate(stores):
@@ -307,7 +339,7 @@ def run_glv(args):
         for _ in range(args.warmup):
             step(ix)
         torch.cuda.synchronize()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -325,18 +357,14 @@ def run_glv(args):
             clocks = sampler.summary()
         if world > 1:
             dist.barrier()
-        per_step = [evs[s][0].elapsed_time(evs[s][4]) for s in range(args.steps)]
-        kern = [[evs[s][t].elapsed_time(evs[s][t + 1]) for s in range(args.steps)] for t in range(4)]
-        tot_ms = sum(per_step)
-        if world > 1:
-            t = torch.tensor([tot_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot_ms = float(t.item())
+        per_step = [evs[s][0].elapsed_time(evs[s][3]) for s in range(args.steps)]
+        kern = [[evs[s][t].elapsed_time(evs[s][t + 1]) for s in range(args.steps)] for t in range(3)]
+        tot_ms = max_over_ranks(sum(per_step))
         assert ix.device_status() == 0, "device reported an error during the bench"
         results[st] = dict(ms_per_step=tot_ms / args.steps,
-                           value=world * nq * args.steps / (tot_ms / 1e3),
+                           value=job_throughput(nq * args.steps, world, tot_ms),
                            kernels_ms={n: statistics.mean(v) for n, v in
-                                       zip(("project", "score", "topk", "rerank"), kern)},
+                                       zip(("project", "score_topk", "rerank"), kern)},
                            wall_s=wall)
 
     # ---- end-to-end through the public host API (pinned host buffers, copies timed) ----
@@ -360,11 +388,7 @@ def run_glv(args):
         e1.record()
         e1.synchronize()
         e_ms.append(e0.elapsed_time(e1))
-    e2e_ms = sum(e_ms) / len(e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(sum(e_ms) / len(e_ms))
     h2d = Qh.numel() * 4 + offh.numel() * 8 + idsh.numel() * 4
     d2h = outs.numel() * 4 + outi.numel() * 4
 
@@ -408,9 +432,9 @@ def run_glv(args):
     eb = glv.elem_bytes(glv.DTYPES[args.store])
     bytes_per_cand = d * eb + (4 if args.store == "fp8" else 0) + 4
     alg_bytes = total * bytes_per_cand
-    score_ms = head["kernels_ms"]["score"]
+    score_ms = head["kernels_ms"]["score_topk"]
     achieved = alg_bytes / (score_ms / 1e3) / 1e9
-    traffic = recorded_traffic("paper_2410_22347_gb300/csrc/score.cu", args.workload, args.store)
+    traffic = recorded_traffic(args.workload, args.store)
     rec = line_extra.get("recall_10at10_vs_oracle", {}).get(args.store)
     line = {
         "metric": METRIC,
@@ -425,16 +449,17 @@ def run_glv(args):
         "vs_baseline": None,
         "dtype": args.store,
         "data": "synthetic",
-        "config": {"workload": args.workload, "N": int(w.X.shape[0]), "D": D, "d": d, "C": C,
+        "config": {"workload": args.workload, "overrides": args.overrides or None, "N": int(w.X.shape[0]), "D": D, "d": d, "C": C,
                    "queries_per_gpu": nq, "candidates_per_query": total // nq, "kappa": w.kappa, "k": w.k,
-                   "reduced_row_store": args.store, "accumulate": "f32", "projection": "f32",
+                   "reduced_row_store": args.store, "accumulate": "f32",
+                   "projection": {0: "f32 (tcgen05 3xTF32)", 1: "bf16 (tcgen05)"}[idx[args.store].compute],
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "glv_score_candidates", "bound": "hbm", "achieved": achieved, "peak": hbm,
+        "roofline": {"kernel": "glv_score_topk (score_topk_kernel)", "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs",
                      "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                      "bytes_per_candidate": bytes_per_cand, "kernel_ms": score_ms},
         "kernels_ms": head["kernels_ms"],
-        "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_throughput(nq, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,

@@ -135,14 +135,25 @@ glv_status glv_build_reduced_noalloc(const float* X, int64_t N, int32_t D, const
 /* ---------------------------------------------------------------------------------------
  * Query preprocessing of Algorithm 4 (eager):  q_{j,c} = A_c q_j  for every c = 1..C,
  * i.e. one dense GEMM  Qp = Q . [A_1; ...; A_C]^T  of shape nq x (C*d).
- *   Q       : nq x D float32.           A : C x d x D float32.
- *   compute : GLV_F32 -- FP32 products and sums (matches an FP64 reference to ~1e-6
- *             relative); GLV_BF16 -- operands rounded to bfloat16, FP32 accumulation.
- *   Qp      : nq x C x d float32 output (row j holds the C projected views of q_j).
+ *   Q         : nq x D float32.           A : C x d x D float32.
+ *   compute   : GLV_F32  -- FP32-accurate.  With a workspace: tcgen05 tensor cores, each
+ *                           operand split exactly into TF32 hi + lo and three MMAs per step
+ *                           (hi*hi + hi*lo + lo*hi), ~1e-7 relative; with workspace == NULL:
+ *                           a SIMT FP32 FMA kernel (slower, no workspace needed).
+ *               GLV_BF16 -- operands rounded to bfloat16, FP32 accumulation on tcgen05
+ *                           (workspace required).
+ *   Qp        : nq x C x d float32 output (row j holds the C projected views of q_j).
+ *   workspace : NULL (GLV_F32 only) or device scratch of
+ *               glv_project_queries_workspace_size(nq, D, C, d, compute) bytes, 256-byte
+ *               aligned, holding the converted operands; contents on entry do not matter.
+ *   d_status  : optional device error word; GLV_ERR_TIMEOUT if a bounded device-side wait
+ *               of the tensor-core kernel ran out (the output is then incomplete).
  * ------------------------------------------------------------------------------------- */
+size_t glv_project_queries_workspace_size(int64_t nq, int32_t D, int32_t C, int32_t d,
+                                          glv_dtype compute);
 glv_status glv_project_queries(const float* Q, int64_t nq, int32_t D, const float* A,
                                int32_t C, int32_t d, glv_dtype compute, float* Qp,
-                               void* stream);
+                               void* workspace, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Candidate scoring, Algorithm 4 procedure inner-product and Eq. (GleanVec approximation):
@@ -163,6 +174,22 @@ glv_status glv_score_candidates(const float* Qp, int64_t nq, int32_t C, int32_t 
                                 glv_dtype dt, const uint16_t* tags, int64_t N,
                                 const int64_t* cand_off, const int32_t* cand_ids,
                                 float* scores, int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Fused candidate scoring + top-kappa: the same computation and the same results (bit for
+ * bit) as glv_score_candidates followed by glv_topk, without writing the scores to memory:
+ * one CTA per query keeps them on chip and selects the kappa best there.
+ *   Arguments as for glv_score_candidates and glv_topk.
+ *   scores_scratch : cand_off[nq] float32 scratch.  Used for lists longer than 2048
+ *                    candidates and when nq is small (the lists are then split over many
+ *                    CTAs and the selection runs afterwards); otherwise left untouched.
+ *   out_s, out_id  : nq x kappa outputs, as glv_topk.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, const void* Xred,
+                          int64_t row_stride, const float* scales, glv_dtype dt,
+                          const uint16_t* tags, int64_t N, const int64_t* cand_off,
+                          const int32_t* cand_ids, int32_t kappa, float* scores_scratch,
+                          float* out_s, int32_t* out_id, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Per-query top-kappa of the scores (Algorithm 1: the main step hands kappa candidates to

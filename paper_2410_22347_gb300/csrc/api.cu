@@ -25,10 +25,49 @@ static bool valid_dt(int dt) { return dt == GLV_F32 || dt == GLV_BF16 || dt == G
 
 using namespace glv;
 
+namespace {
 #define GLV_CHECK(cond, code) \
   do {                        \
     if (!(cond)) return code; \
   } while (0)
+static glv_status fill_score_args(ScoreArgs& a, const float* Qp, int64_t nq, int32_t C, int32_t d,
+                                  const void* Xred, int64_t row_stride, const float* scales, glv_dtype dt,
+                                  const uint16_t* tags, int64_t N, const int64_t* cand_off,
+                                  const int32_t* cand_ids, float* scores, int32_t* d_status) {
+  GLV_CHECK(nq >= 0 && C >= 1 && C <= 65536 && d >= 1 && N >= 0 && valid_dt(dt), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(row_stride >= glv_min_row_stride(d, dt) && row_stride % 16 == 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK((dt == GLV_FP8_E4M3) == (scales != nullptr), GLV_ERR_INVALID_ARG);
+  if (nq == 0) return GLV_OK;
+  GLV_CHECK(Qp && cand_off && tags && Xred && cand_ids && scores, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(aligned(Xred, 16), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(nq <= kMaxGridX, GLV_ERR_UNSUPPORTED);
+  const int eb = elem_bytes(dt);
+  const int epc = 16 / eb;
+  const int64_t dpad = ((int64_t)d + epc - 1) / epc * epc;
+  GLV_CHECK((size_t)C * (dpad + 4) * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
+  const int64_t bytes = (int64_t)d * eb;
+  const int nch = (int)((bytes + 15) / 16);
+  GLV_CHECK(nch <= 32 * 8, GLV_ERR_UNSUPPORTED);
+  a.Qp = Qp;
+  a.C = C;
+  a.d = d;
+  a.qstride = 0;
+  a.Xred = static_cast<const uint8_t*>(Xred);
+  a.row_stride = row_stride;
+  a.scales = scales;
+  a.tags = tags;
+  a.N = N;
+  a.off = cand_off;
+  a.ids = cand_ids;
+  a.scores = scores;
+  a.d_status = d_status;
+  a.nch = nch;
+  a.tail = (int)(bytes - (int64_t)(nch - 1) * 16);
+  a.splits = 1;
+  return GLV_OK;
+}
+
+}  // namespace
 
 #define GLV_LAUNCH(expr)                            \
   do {                                              \
@@ -91,17 +130,30 @@ glv_status glv_build_reduced(const float* X, int64_t N, int32_t D, const uint16_
   return GLV_OK;
 }
 
+size_t glv_project_queries_workspace_size(int64_t nq, int32_t D, int32_t C, int32_t d,
+                                          glv_dtype compute) {
+  if (nq < 0 || D < 1 || C < 1 || d < 1 || (compute != GLV_F32 && compute != GLV_BF16)) return 0;
+  return project_tc_ws_bytes(nq, D, (int64_t)C * d, compute == GLV_BF16);
+}
+
 glv_status glv_project_queries(const float* Q, int64_t nq, int32_t D, const float* A,
                                int32_t C, int32_t d, glv_dtype compute, float* Qp,
-                               void* stream) {
+                               void* workspace, int32_t* d_status, void* stream) {
   GLV_CHECK(nq >= 0 && D >= 1 && C >= 1 && C <= 65536 && d >= 1 && d <= D, GLV_ERR_INVALID_ARG);
   GLV_CHECK(compute == GLV_F32 || compute == GLV_BF16, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(compute == GLV_F32 || workspace != nullptr, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(workspace == nullptr || aligned(workspace, 256), GLV_ERR_INVALID_ARG);
   if (nq == 0) return GLV_OK;
   GLV_CHECK(Q && A && Qp, GLV_ERR_INVALID_ARG);
   const int64_t M = (int64_t)C * d;
-  GLV_CHECK(M <= 2147483647LL && nq <= 65535LL * 128, GLV_ERR_UNSUPPORTED);
-  if (compute == GLV_BF16) return GLV_ERR_UNSUPPORTED;  // tensor-core path not in this build
-  GLV_LAUNCH(launch_project_simt(Q, nq, D, A, M, Qp, (cudaStream_t)stream));
+  GLV_CHECK(M <= 2147483647LL && nq <= 2147483647LL, GLV_ERR_UNSUPPORTED);
+  if (workspace == nullptr) {  // exact FP32 FMA path (no workspace needed)
+    GLV_CHECK(nq <= 65535LL * 128, GLV_ERR_UNSUPPORTED);
+    GLV_LAUNCH(launch_project_simt(Q, nq, D, A, M, Qp, (cudaStream_t)stream));
+    return GLV_OK;
+  }
+  GLV_LAUNCH(launch_project_tc(Q, nq, D, A, M, Qp, compute == GLV_BF16, workspace, d_status, num_sms(),
+                               (cudaStream_t)stream));
   return GLV_OK;
 }
 
@@ -110,39 +162,27 @@ glv_status glv_score_candidates(const float* Qp, int64_t nq, int32_t C, int32_t 
                                 glv_dtype dt, const uint16_t* tags, int64_t N,
                                 const int64_t* cand_off, const int32_t* cand_ids,
                                 float* scores, int32_t* d_status, void* stream) {
-  GLV_CHECK(nq >= 0 && C >= 1 && C <= 65536 && d >= 1 && N >= 0 && valid_dt(dt),
-            GLV_ERR_INVALID_ARG);
-  GLV_CHECK(row_stride >= glv_min_row_stride(d, dt) && row_stride % 16 == 0, GLV_ERR_INVALID_ARG);
-  GLV_CHECK((dt == GLV_FP8_E4M3) == (scales != nullptr), GLV_ERR_INVALID_ARG);
-  if (nq == 0) return GLV_OK;
-  GLV_CHECK(Qp && cand_off && tags && Xred && cand_ids && scores, GLV_ERR_INVALID_ARG);
-  GLV_CHECK(aligned(Xred, 16), GLV_ERR_INVALID_ARG);
-  GLV_CHECK(nq <= kMaxGridX, GLV_ERR_UNSUPPORTED);
-  const int eb = elem_bytes(dt);
-  const int epc = 16 / eb;
-  const int64_t dpad = ((int64_t)d + epc - 1) / epc * epc;
-  GLV_CHECK((size_t)C * (dpad + 4) * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
-  const int64_t bytes = (int64_t)d * eb;
-  const int nch = (int)((bytes + 15) / 16);
-  GLV_CHECK(nch <= 32 * 8, GLV_ERR_UNSUPPORTED);
   ScoreArgs a;
-  a.Qp = Qp;
-  a.C = C;
-  a.d = d;
-  a.qstride = 0;
-  a.Xred = static_cast<const uint8_t*>(Xred);
-  a.row_stride = row_stride;
-  a.scales = scales;
-  a.tags = tags;
-  a.N = N;
-  a.off = cand_off;
-  a.ids = cand_ids;
-  a.scores = scores;
-  a.d_status = d_status;
-  a.nch = nch;
-  a.tail = (int)(bytes - (int64_t)(nch - 1) * 16);
-  a.splits = 1;
+  const glv_status st = fill_score_args(a, Qp, nq, C, d, Xred, row_stride, scales, dt, tags, N, cand_off,
+                                        cand_ids, scores, d_status);
+  if (st != GLV_OK || nq == 0) return st;
   GLV_LAUNCH(launch_score(a, dt, nq, num_sms(), (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, const void* Xred,
+                          int64_t row_stride, const float* scales, glv_dtype dt,
+                          const uint16_t* tags, int64_t N, const int64_t* cand_off,
+                          const int32_t* cand_ids, int32_t kappa, float* scores_scratch,
+                          float* out_s, int32_t* out_id, int32_t* d_status, void* stream) {
+  GLV_CHECK(kappa >= 1 && kappa <= GLV_MAX_KAPPA, GLV_ERR_INVALID_ARG);
+  ScoreArgs a;
+  const glv_status st = fill_score_args(a, Qp, nq, C, d, Xred, row_stride, scales, dt, tags, N, cand_off,
+                                        cand_ids, scores_scratch, d_status);
+  if (st != GLV_OK || nq == 0) return st;
+  GLV_CHECK(out_s && out_id, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(fused_smem_bytes(C, d, dt) <= kSmemLimit - 12 * 1024, GLV_ERR_UNSUPPORTED);  // + static TopkSmem
+  GLV_LAUNCH(launch_score_topk(a, dt, nq, kappa, out_s, out_id, num_sms(), (cudaStream_t)stream));
   return GLV_OK;
 }
 

@@ -36,12 +36,18 @@ struct RerankArgs {
 };
 
 cudaError_t launch_score(const ScoreArgs& a, int dt, int64_t nq, int num_sms, cudaStream_t st);
+size_t fused_smem_bytes(int C, int d, int dt);
+cudaError_t launch_score_topk(const ScoreArgs& a, int dt, int64_t nq, int kappa, float* out_s,
+                              int32_t* out_id, int num_sms, cudaStream_t st);
 cudaError_t launch_topk(const float* scores, const int64_t* off, const int32_t* ids, int64_t nq,
                         int kappa, float* out_s, int32_t* out_id, cudaStream_t st);
 cudaError_t launch_rerank(const RerankArgs& a, int64_t nq, bool vec, cudaStream_t st);
 size_t rerank_smem_bytes(int D, int kappa);
 cudaError_t launch_project_simt(const float* Q, int64_t nq, int D, const float* A, int64_t Mcols,
                                 float* Qp, cudaStream_t st);
+size_t project_tc_ws_bytes(int64_t nq, int D, int64_t Mc, int bf16);
+cudaError_t launch_project_tc(const float* Q, int64_t nq, int D, const float* A, int64_t Mc, float* Qp,
+                              int bf16, void* ws, int32_t* d_status, int num_sms, cudaStream_t st);
 size_t build_ws_bytes(int64_t N, int C);
 cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags, const float* B,
                          int C, int d, int dt, void* Xred, int64_t row_stride, float* scales,

@@ -1,0 +1,172 @@
+// score_dev.cuh -- device-side body of the gather-score (Algorithm 4, procedure
+// inner-product; Eq. GleanVec approximation, Section 4), shared by the stand-alone scoring
+// kernel and the fused score + top-kappa kernel so both compute bit-identical scores.
+//
+// A group of G lanes scores one candidate: the lanes issue all of their 16-byte loads of
+// the reduced row (NCH each) before any arithmetic, so a warp keeps 32 x NCH x 16 bytes in
+// flight; partial dots are combined with xor-shuffles inside the group.  Rows are decoded in
+// registers: FP32 as is, BF16 by shifting into the high half of an FP32 word, FP8-e4m3 by
+// moving sign / exponent / mantissa bits into an FP32 word, which yields
+// decode(code) * 2^-120 for normal and subnormal codes alike; the 2^120 factor and the row
+// scale are applied once to the finished dot.
+#pragma once
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace glv {
+
+template <int DT>
+struct Elem;
+template <>
+struct Elem<GLV_F32> {
+  static constexpr int kPerChunk = 4;
+  static constexpr int kBytes = 4;
+};
+template <>
+struct Elem<GLV_BF16> {
+  static constexpr int kPerChunk = 8;
+  static constexpr int kBytes = 2;
+};
+template <>
+struct Elem<GLV_FP8_E4M3> {
+  static constexpr int kPerChunk = 16;
+  static constexpr int kBytes = 1;
+};
+
+// FP8-e4m3 byte (bits 24..31 of t) -> FP32 word with the same sign, the 4 exponent bits as
+// the low bits of the FP32 exponent field and the 3 mantissa bits on top of the FP32
+// mantissa: value = decode(byte) * 2^-120 (exact, including subnormal codes).
+GLV_DEV float e4m3_hi_byte_scaled(uint32_t t) {
+  return __uint_as_float((t & 0x80000000u) | ((t & 0x7f000000u) >> 4));
+}
+
+template <int DT>
+GLV_DEV float dot_chunk(uint4 v, const float* q) {
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  if constexpr (DT == GLV_F32) {
+    float4 a = q4[0];
+    return a.x * __uint_as_float(v.x) + a.y * __uint_as_float(v.y) + a.z * __uint_as_float(v.z) +
+           a.w * __uint_as_float(v.w);
+  } else if constexpr (DT == GLV_BF16) {
+    float4 a = q4[0], b = q4[1];
+    float s = a.x * __uint_as_float(v.x << 16);
+    s = fmaf(a.y, __uint_as_float(v.x & 0xffff0000u), s);
+    s = fmaf(a.z, __uint_as_float(v.y << 16), s);
+    s = fmaf(a.w, __uint_as_float(v.y & 0xffff0000u), s);
+    s = fmaf(b.x, __uint_as_float(v.z << 16), s);
+    s = fmaf(b.y, __uint_as_float(v.z & 0xffff0000u), s);
+    s = fmaf(b.z, __uint_as_float(v.w << 16), s);
+    s = fmaf(b.w, __uint_as_float(v.w & 0xffff0000u), s);
+    return s;
+  } else {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    float s = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float4 a = q4[t];
+      s = fmaf(a.x, e4m3_hi_byte_scaled(w[t] << 24), s);
+      s = fmaf(a.y, e4m3_hi_byte_scaled(w[t] << 16), s);
+      s = fmaf(a.z, e4m3_hi_byte_scaled(w[t] << 8), s);
+      s = fmaf(a.w, e4m3_hi_byte_scaled(w[t]), s);
+    }
+    return s;
+  }
+}
+
+// Zero the bytes at and beyond `nbytes` (0 < nbytes < 16) of a 16-byte chunk.
+GLV_DEV uint4 keep_bytes(uint4 v, int nbytes) {
+  uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int b = nbytes - 4 * t;
+    if (b <= 0) w[t] = 0u;
+    else if (b < 4) w[t] &= (1u << (8 * b)) - 1u;
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+
+
+// Stage the C projected views of query j into shared memory, zero padded to a.qstride.
+GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
+  const float* qj = a.Qp + j * (int64_t)a.C * a.d;
+  const int total = a.C * a.qstride;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int c = t / a.qstride, r = t - c * a.qstride;
+    qs[t] = (r < a.d) ? qj[(int64_t)c * a.d + r] : 0.f;
+  }
+}
+
+// Score candidates p in [b0, b1) with the CTA's warps; sink(p, score) receives each score
+// (from lane 0 of the candidate's lane group).  A bad id or tag scores -inf and is reported.
+template <int DT, int G, int NCH, class Sink>
+GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_t b1, Sink sink) {
+  constexpr int EPC = Elem<DT>::kPerChunk;
+  constexpr int GPW = kWarp / G;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int g = lane / G, gl = lane % G;
+
+  const int64_t step = (int64_t)nwarps * GPW;
+  int64_t base = b0 + (int64_t)warp * GPW;
+  // the id of the next candidate is loaded one iteration ahead, so the row loads of an
+  // iteration do not wait for an id round trip
+  int64_t id_next = (base + g < b1) ? (int64_t)__ldg(a.ids + base + g) : 0;
+  for (; base < b1; base += step) {
+    const int64_t p = base + g;
+    const bool in = p < b1;
+    const int64_t id = id_next;
+    id_next = (p + step < b1) ? (int64_t)__ldg(a.ids + p + step) : 0;
+    bool ok = in && id >= 0 && id < a.N;
+    int tag = ok ? (int)__ldg(a.tags + id) : 0;
+    if (ok && tag >= a.C) ok = false;
+
+    uint4 v[NCH];
+    const uint8_t* row = a.Xred + id * a.row_stride;
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+      const int ch = gl + t * G;
+      v[t] = (ok && ch < a.nch) ? ld_stream_v4(row + (int64_t)ch * 16) : make_uint4(0, 0, 0, 0);
+    }
+    float sc = 1.f;
+    if constexpr (DT == GLV_FP8_E4M3) sc = ok ? __ldg(a.scales + id) : 0.f;
+
+    float acc = 0.f;
+    const float* qrow = qs + tag * a.qstride;
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+      const int ch = gl + t * G;
+      if (ch < a.nch) {
+        uint4 x = v[t];
+        if (ch == a.nch - 1 && a.tail < 16) x = keep_bytes(x, a.tail);
+        acc += dot_chunk<DT>(x, qrow + ch * EPC);
+      }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+
+    if (in && gl == 0) {
+      float s;
+      if (!ok) {
+        s = -INFINITY;
+        report(a.d_status, GLV_ERR_BAD_ID);
+      } else if constexpr (DT == GLV_FP8_E4M3) {
+        s = (acc * 0x1p120f) * sc;
+      } else {
+        s = acc;
+      }
+      sink(p, s);
+    }
+  }
+}
+
+// Lanes per candidate for a row of nch 16-byte chunks: the dtype's default group size when
+// that needs at most 8 loads per lane, else 32 lanes.
+template <int DT>
+constexpr int default_group() {
+  return (DT == GLV_F32) ? 8 : (DT == GLV_BF16 ? 4 : 2);
+}
+
+}  // namespace glv

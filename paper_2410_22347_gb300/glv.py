@@ -43,8 +43,10 @@ def _load() -> ctypes.CDLL:
         "glv_build_reduced_workspace_size": (sz, [i64, i32]),
         "glv_build_reduced": (i32, [P, i64, i32, P, P, i32, i32, i32, P, i64, P, P, P, P]),
         "glv_build_reduced_noalloc": (i32, [P, i64, i32, P, P, i32, i32, i32, P, i64, P, P, P]),
-        "glv_project_queries": (i32, [P, i64, i32, P, i32, i32, i32, P, P]),
+        "glv_project_queries_workspace_size": (sz, [i64, i32, i32, i32, i32]),
+        "glv_project_queries": (i32, [P, i64, i32, P, i32, i32, i32, P, P, P, P]),
         "glv_score_candidates": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P]),
+        "glv_score_topk": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, i32, P, P, P, P, P]),
         "glv_topk": (i32, [P, P, P, i64, i32, P, P, P]),
         "glv_rerank": (i32, [P, i64, i32, P, i64, P, i32, i32, P, P, P, P]),
     }
@@ -159,15 +161,26 @@ def glv_build_reduced_noalloc(X, tags, B, dt: int, Xred, row_stride: int, scales
     return Xred, scales
 
 
-def glv_project_queries(Q, A, compute: int = GLV_F32, Qp=None, stream=None):
+def project_workspace_bytes(nq: int, D: int, C: int, d: int, compute: int) -> int:
+    return int(_lib.glv_project_queries_workspace_size(nq, D, C, d, compute))
+
+
+def glv_project_queries(Q, A, compute: int = GLV_F32, Qp=None, workspace=None, d_status=None,
+                        stream=None, tensor_cores: bool = True):
+    """Qp = Q . [A_1; ...; A_C]^T.  With tensor_cores (default) a workspace is allocated if not
+    given; tensor_cores=False with compute=GLV_F32 selects the SIMT FP32 kernel."""
     _need(Q, torch.float32, "Q", 2)
     _need(A, torch.float32, "A", 3)
     nq, D = Q.shape
     C, d, _ = A.shape
     if Qp is None:
         Qp = torch.empty(nq, C, d, dtype=torch.float32, device=Q.device)
+    if workspace is None and (tensor_cores or compute != GLV_F32):
+        workspace = torch.empty(max(project_workspace_bytes(nq, D, C, d, compute), 1), dtype=torch.uint8,
+                                device=Q.device)
     _check("glv_project_queries",
-           _lib.glv_project_queries(_ptr(Q), nq, D, _ptr(A), C, d, compute, _ptr(Qp), _stream(stream)))
+           _lib.glv_project_queries(_ptr(Q), nq, D, _ptr(A), C, d, compute, _ptr(Qp), _ptr(workspace),
+                                    _ptr(d_status), _stream(stream)))
     return Qp
 
 
@@ -187,6 +200,29 @@ def glv_score_candidates(Qp, Xred, row_stride: int, scales, dt: int, tags, off, 
                                      _ptr(tags), N, _ptr(off), _ptr(ids), _ptr(scores),
                                      _ptr(d_status), _stream(stream)))
     return scores
+
+
+def glv_score_topk(Qp, Xred, row_stride: int, scales, dt: int, tags, off, ids, kappa: int, scores_scratch=None,
+                   out_s=None, out_id=None, d_status=None, stream=None, d: int | None = None):
+    """Fused scoring + top-kappa (same results as glv_score_candidates then glv_topk)."""
+    _need(Qp, torch.float32, "Qp", 3)
+    _need(tags, torch.uint16, "tags", 1)
+    _need(off, torch.int64, "cand_off", 1)
+    _need(ids, torch.int32, "cand_ids", 1)
+    nq, C, dq = Qp.shape
+    d = dq if d is None else d
+    N = tags.shape[0]
+    if scores_scratch is None:
+        scores_scratch = torch.empty(max(ids.shape[0], 1), dtype=torch.float32, device=Qp.device)
+    if out_s is None:
+        out_s = torch.empty(nq, kappa, dtype=torch.float32, device=Qp.device)
+    if out_id is None:
+        out_id = torch.empty(nq, kappa, dtype=torch.int32, device=Qp.device)
+    _check("glv_score_topk",
+           _lib.glv_score_topk(_ptr(Qp), nq, C, d, _ptr(Xred), row_stride, _ptr(scales), dt, _ptr(tags), N,
+                               _ptr(off), _ptr(ids), kappa, _ptr(scores_scratch), _ptr(out_s), _ptr(out_id),
+                               _ptr(d_status), _stream(stream)))
+    return out_s, out_id
 
 
 def glv_topk(scores, off, ids, kappa: int, out_s=None, out_id=None, stream=None):

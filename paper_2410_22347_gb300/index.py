@@ -4,7 +4,7 @@
 (A_c, B_c) and the reduced store x_i^low = B_{c_i} x_i, and runs the eager multi-step
 search of Algorithm 1 / Algorithm 4 with four library calls:
 
-    glv_project_queries -> glv_score_candidates -> glv_topk -> glv_rerank
+    glv_project_queries -> glv_score_topk (fused scoring + top-kappa) -> glv_rerank
 
 ``search`` takes device tensors; ``search_host`` takes host tensors (pinned when given
 pinned memory), copies them in, searches and copies the top-k back on the same stream.
@@ -19,7 +19,7 @@ from . import glv
 
 class GleanVecIndex:
     def __init__(self, X: torch.Tensor, A: torch.Tensor, B: torch.Tensor, *, tags: torch.Tensor | None = None,
-                 mu: torch.Tensor | None = None, store: str = "bf16", project: str = "f32", stream=None):
+                 mu: torch.Tensor | None = None, store: str = "bf16", project: str | None = None, stream=None):
         if tags is None:
             if mu is None:
                 raise ValueError("give cluster tags or landmarks mu")
@@ -28,7 +28,8 @@ class GleanVecIndex:
         self.N, self.D = X.shape
         self.C, self.d, _ = A.shape
         self.dt = glv.DTYPES[store]
-        self.compute = glv.DTYPES[project]
+        # low-precision stores pair with BF16 projection operands; the FP32 store keeps FP32
+        self.compute = glv.DTYPES[project if project is not None else ("f32" if store == "f32" else "bf16")]
         self.row_stride = glv.min_row_stride(self.d, self.dt)
         self.status = torch.zeros(1, dtype=torch.int32, device=X.device)
         self.Xred, self.scales = glv.glv_build_reduced(X, tags, B, self.dt, d_status=self.status,
@@ -43,6 +44,8 @@ class GleanVecIndex:
             dev = self.X.device
             b = dict(
                 Qp=torch.empty(nq, self.C, self.d, dtype=torch.float32, device=dev),
+                pws=torch.empty(max(glv.project_workspace_bytes(nq, self.D, self.C, self.d, self.compute), 1),
+                                dtype=torch.uint8, device=dev),
                 scores=torch.empty(max(total, 1), dtype=torch.float32, device=dev),
                 ts=torch.empty(nq, kappa, dtype=torch.float32, device=dev),
                 ti=torch.empty(nq, kappa, dtype=torch.int32, device=dev),
@@ -58,13 +61,16 @@ class GleanVecIndex:
         (scores, ids) of shape nq x k.  kappa == 0: no re-rank (top k of reduced scores)."""
         nq = Q.shape[0]
         b = self._buffers(nq, ids.shape[0], max(kappa, k), k)
-        glv.glv_project_queries(Q, self.A, self.compute, Qp=b["Qp"], stream=stream)
-        glv.glv_score_candidates(b["Qp"], self.Xred, self.row_stride, self.scales, self.dt, self.tags, off, ids,
-                                 scores=b["scores"], d_status=self.status, stream=stream)
+        glv.glv_project_queries(Q, self.A, self.compute, Qp=b["Qp"], workspace=b["pws"], d_status=self.status,
+                                stream=stream)
         if kappa <= 0:
-            glv.glv_topk(b["scores"], off, ids, k, out_s=b["fs"], out_id=b["fi"], stream=stream)
+            glv.glv_score_topk(b["Qp"], self.Xred, self.row_stride, self.scales, self.dt, self.tags, off, ids, k,
+                               scores_scratch=b["scores"], out_s=b["fs"], out_id=b["fi"], d_status=self.status,
+                               stream=stream)
             return b["fs"], b["fi"]
-        glv.glv_topk(b["scores"], off, ids, kappa, out_s=b["ts"], out_id=b["ti"], stream=stream)
+        glv.glv_score_topk(b["Qp"], self.Xred, self.row_stride, self.scales, self.dt, self.tags, off, ids, kappa,
+                           scores_scratch=b["scores"], out_s=b["ts"], out_id=b["ti"], d_status=self.status,
+                           stream=stream)
         glv.glv_rerank(self.X, Q, b["ti"], k, out_s=b["fs"], out_id=b["fi"], d_status=self.status,
                        stream=stream)
         return b["fs"], b["fi"]

@@ -100,10 +100,18 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert score(FAKE, 3, 4, 16, FAKE, 64, None, 0, FAKE, 10, None, FAKE, FAKE, None, None) == INV  # null off
     assert score(FAKE, 3, 65536, 1024, FAKE, 4096, None, 0, FAKE, 10, FAKE, FAKE, FAKE, None, None) == 3  # too big for smem
 
-    proj = _ret_i32(lib, "glv_project_queries", [P, i64, i32, P, i32, i32, i32, P, P])
-    assert proj(FAKE, 5, 32, FAKE, 2, 33, 0, FAKE, None) == INV   # d > D
-    assert proj(FAKE, 5, 32, FAKE, 2, 8, 2, FAKE, None) == INV    # FP8 compute not offered
-    assert proj(FAKE, 5, 32, None, 2, 8, 0, FAKE, None) == INV
+    proj = _ret_i32(lib, "glv_project_queries", [P, i64, i32, P, i32, i32, i32, P, P, P, P])
+    assert proj(FAKE, 5, 32, FAKE, 2, 33, 0, FAKE, None, None, None) == INV   # d > D
+    assert proj(FAKE, 5, 32, FAKE, 2, 8, 2, FAKE, None, None, None) == INV    # FP8 compute not offered
+    assert proj(FAKE, 5, 32, None, 2, 8, 0, FAKE, None, None, None) == INV
+    assert proj(FAKE, 5, 32, FAKE, 2, 8, 1, FAKE, None, None, None) == INV    # BF16 needs a workspace
+    assert proj(FAKE, 5, 32, FAKE, 2, 8, 1, FAKE, P(4096 + 16), None, None) == INV  # misaligned workspace
+    lib.glv_project_queries_workspace_size.restype = ctypes.c_size_t
+    lib.glv_project_queries_workspace_size.argtypes = [i64, i32, i32, i32, i32]
+    # BF16: (nq + C*d) rows x 64-padded K x 2 bytes, each operand rounded to 1 KB
+    assert lib.glv_project_queries_workspace_size(10000, 768, 32, 160, 1) == 10000 * 768 * 2 + 5120 * 768 * 2
+    # FP32 (TF32 hi/lo): K padded to 128; Q 100 x 128 x 4 B and A 16 x 128 x 4 B, two copies each
+    assert lib.glv_project_queries_workspace_size(100, 100, 2, 8, 0) == 2 * 51200 + 2 * 8192
 
     tags = _ret_i32(lib, "glv_assign_tags", [P, i64, i32, P, i32, P, P])
     assert tags(FAKE, 10, 8, FAKE, 0, FAKE, None) == INV

@@ -183,14 +183,36 @@ def test_build_reduced_fp8(glv, D, d, C):
 # Algorithm 4 preprocess: projection GEMM
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("nq,D,d,C,orth", [(23, 96, 27, 5, True), (300, 768, 160, 32, True),
-                                          (129, 130, 33, 3, False), (1, 7, 3, 2, False),
-                                          (257, 512, 128, 8, True)])
-def test_project_queries_f32(glv, nq, D, d, C, orth):
+PROJ_CASES = [(23, 96, 27, 5, True), (300, 768, 160, 32, True), (129, 130, 33, 3, False), (1, 7, 3, 2, False),
+              (257, 512, 128, 8, True), (2000, 768, 160, 32, True), (700, 200, 96, 4, False)]
+
+
+@pytest.mark.parametrize("tensor_cores", [False, True], ids=["simt", "tcgen05-3xtf32"])
+@pytest.mark.parametrize("nq,D,d,C,orth", PROJ_CASES)
+def test_project_queries_f32(glv, nq, D, d, C, orth, tensor_cores):
     rng, X, Q, mu, A, B, tags = _problem(nq + D, N=10, D=D, d=d, C=C, nq=nq, orth=orth)
     ref = oracle.project(Q, A)
-    got = glv.glv_project_queries(_t(Q), _t(A)).cpu().numpy()
+    st = _status()
+    got = glv.glv_project_queries(_t(Q), _t(A), glv.GLV_F32, d_status=st, tensor_cores=tensor_cores).cpu().numpy()
+    assert st.item() == 0
     scale = np.linalg.norm(A, axis=2)[None] * np.linalg.norm(Q, axis=1)[:, None, None]
+    ok, worst, bad = scores_close(got, ref, scale, TOL)
+    assert ok, f"worst {worst}"
+
+
+@pytest.mark.parametrize("nq,D,d,C,orth", PROJ_CASES)
+def test_project_queries_bf16(glv, nq, D, d, C, orth):
+    """BF16 operands: the product of two BF16 values is exact in FP32, so the tensor-core
+    result must match the oracle run on the BF16-rounded operands to FP32 accumulation
+    accuracy."""
+    rng, X, Q, mu, A, B, tags = _problem(nq + D + 7, N=10, D=D, d=d, C=C, nq=nq, orth=orth)
+    Qb = oracle.bf16_decode(oracle.bf16_encode(Q)).astype(np.float32)
+    Ab = oracle.bf16_decode(oracle.bf16_encode(A)).astype(np.float32)
+    ref = oracle.project(Qb, Ab)
+    st = _status()
+    got = glv.glv_project_queries(_t(Q), _t(A), glv.GLV_BF16, d_status=st).cpu().numpy()
+    assert st.item() == 0
+    scale = np.linalg.norm(Ab, axis=2)[None] * np.linalg.norm(Qb, axis=1)[:, None, None]
     ok, worst, bad = scores_close(got, ref, scale, TOL)
     assert ok, f"worst {worst}"
 
@@ -346,7 +368,7 @@ def _pipeline(glv, X, Q, A, B, tags, off, ids, kappa, k, dt):
     st = _status()
     Xt, Qt, tt = _t(X), _t(Q), _t(tags)
     Xred, scales = glv.glv_build_reduced(Xt, tt, _t(B), dt, d_status=st)
-    Qp = glv.glv_project_queries(Qt, _t(A))
+    Qp = glv.glv_project_queries(Qt, _t(A), glv.GLV_F32 if dt == glv.GLV_F32 else glv.GLV_BF16, d_status=st)
     rs = glv.min_row_stride(A.shape[1], dt)
     sc = glv.glv_score_candidates(Qp, Xred, rs, scales, dt, tt, _t(off), _t(ids), d_status=st)
     ts, ti = glv.glv_topk(sc, _t(off), _t(ids), kappa)
@@ -393,3 +415,67 @@ def test_search_pipeline_low_precision_recall(glv, dt_name):
     ref_s, ref_id = oracle.search(X, Xr, tags, A, Q, off, ids, w.kappa, w.k)
     fs, fi = _pipeline(glv, X, Q, A, B, tags, off, ids, w.kappa, w.k, glv.DTYPES[dt_name])
     assert oracle.recall(fi, ref_id) >= 0.9
+
+
+# ---------------------------------------------------------------------------------------
+# fused scoring + top-kappa: bit-identical to the two-kernel path
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("nq,kappa", [(700, 100), (700, 1), (650, 1024), (40, 100)])
+def test_score_topk_fused_matches_separate(glv, dt_name, nq, kappa):
+    dt = glv.DTYPES[dt_name]
+    rng, X, Q, mu, A, B, tags = _problem(nq + kappa, N=6000, D=96, d=40, C=7, nq=nq)
+    lens = rng.integers(0, 3000, nq)
+    lens[:5] = [0, 1, kappa, 2048, 2049]          # empty, single, exactly kappa, cache edge, spill
+    lists = _ragged_lists(rng, nq, len(X), lens)
+    lists[7] = np.concatenate([lists[7][:10], [len(X) + 5]])  # a bad id
+    off, ids = _csr(lists)
+    st = _status()
+    Xt, tt = _t(X), _t(tags)
+    Xred, scales = glv.glv_build_reduced(Xt, tt, _t(B), dt)
+    Qp = glv.glv_project_queries(_t(Q), _t(A), glv.GLV_F32)
+    rs = glv.min_row_stride(40, dt)
+    offt, idst = _t(off), _t(ids)
+    sc = glv.glv_score_candidates(Qp, Xred, rs, scales, dt, tt, offt, idst, d_status=st)
+    ts, ti = glv.glv_topk(sc, offt, idst, kappa)
+    st2 = _status()
+    fs, fi = glv.glv_score_topk(Qp, Xred, rs, scales, dt, tt, offt, idst, kappa, d_status=st2)
+    torch.cuda.synchronize()
+    assert st.item() == glv.GLV_ERR_BAD_ID and st2.item() == glv.GLV_ERR_BAD_ID
+    np.testing.assert_array_equal(fi.cpu().numpy(), ti.cpu().numpy())
+    np.testing.assert_array_equal(fs.cpu().numpy().view(np.uint32), ts.cpu().numpy().view(np.uint32))
+    # and the separate path against the oracle's top-kappa of the same FP32 scores
+    ref_s, ref_id = oracle.topk(sc.cpu().numpy().astype(np.float64), off, ids, kappa)
+    np.testing.assert_array_equal(ti.cpu().numpy(), ref_id)
+
+
+def test_index_search_matches_oracle(glv):
+    """The public index API (projection -> fused score/top-kappa -> re-rank) on a workload with
+    enough queries for the fused kernel."""
+    from paper_2410_22347_gb300 import synth
+    from paper_2410_22347_gb300.index import GleanVecIndex
+    w = synth.make_workload(N=30000, D=128, d=32, C=9, nq=800, K_db=12, cands=1000, kappa=50, k=10, cfg=86)
+    X, Q, mu, A, B = (t.numpy() for t in (w.X, w.Q, w.mu, w.A, w.B))
+    off, ids = w.off.numpy(), w.ids.numpy()
+    tags = oracle.assign_tags(X, mu)
+    Xr = oracle.build_reduced(X, tags, B)
+    ref_s, ref_id = oracle.search(X, Xr, tags, A, Q, off, ids, w.kappa, w.k)
+    red, _ = oracle.score(oracle.project(Q, A), Xr, tags, off, ids)
+    kap, _ = oracle.topk(red, off, ids, w.kappa)
+    ix = GleanVecIndex(_t(X), _t(A), _t(B), tags=_t(tags), store="f32")
+    fs, fi = ix.search(_t(Q), _t(off), _t(ids), w.kappa, w.k)
+    torch.cuda.synchronize()
+    assert ix.device_status() == 0
+    fi = fi.cpu().numpy()
+    for j in range(len(Q)):
+        lst = ids[off[j]:off[j + 1]]
+        rd = dict(zip(lst.tolist(), red[off[j]:off[j + 1]].tolist()))
+        ok, why = search_equivalent(fi[j], ref_id[j], ref_s[j],
+                                    lambda i: float(Q[j].astype(np.float64) @ X[i].astype(np.float64)),
+                                    lambda i: rd[i], kap[j, -1], TIE, TIE)
+        assert ok, f"query {j}: {why}"
+    # host-in / host-out path gives the same answer
+    hs, hi = ix.search_host(w.Q.pin_memory(), w.off.pin_memory(), w.ids.pin_memory(), w.kappa, w.k)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hi.numpy(), fi)
