@@ -192,6 +192,20 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
                           float* out_s, int32_t* out_id, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Scoring configuration (the autotuner's hook; no counterpart in the paper).  Per store
+ * type: how many lanes of a warp cooperate on one candidate row (1, 2, 4, 8, 16 or 32;
+ * 0 = library default) and whether the next candidate's row loads are issued before the
+ * current one is computed (pipelined != 0).  The choice changes only speed and the order in
+ * which a row's partial dots are summed (FP32 rounding); glv_score_candidates and
+ * glv_score_topk always use the same configuration, so their results stay identical.  A
+ * choice that cannot serve a row width falls back to the default for that width.
+ * glv_get_score_config reports the configuration used for rows of width d.  Process-wide.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t pipelined);
+glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate,
+                                int32_t* pipelined);
+
+/* ---------------------------------------------------------------------------------------
  * Per-query top-kappa of the scores (Algorithm 1: the main step hands kappa candidates to
  * the post-processing).  Exact selection (radix select on order-preserving keys), output
  * sorted by score descending, ties to the smaller id, NaN last, padding (-inf, -1) when a

@@ -1,0 +1,99 @@
+"""Autotuner for the gather-score kernels.
+
+The scoring kernels are instantiated for several lanes-per-candidate group sizes, with and
+without software pipelining of the row loads (see csrc/score_launch.cuh).  Which one keeps
+HBM busiest depends on the row width, the store type, the candidate-list lengths and the
+GPU, so ``tune_score`` times every offered configuration of the fused score + top-kappa
+call on the caller's own workload (CUDA events on the launching stream, L2 evicted between
+repetitions), installs the fastest through ``glv_set_score_config`` and caches it in a JSON
+file keyed by GPU name, store type, row width, cluster count and mean list length.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import glv
+
+CACHE = os.environ.get("GLV_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "glv", "autotune.json"))
+
+
+def _key(dt: int, d: int, C: int, mean_len: float) -> str:
+    name = torch.cuda.get_device_name()
+    return f"{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
+
+
+def _load_cache() -> dict:
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save_cache(c: dict) -> None:
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(c, f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE)
+    except OSError:
+        pass
+
+
+def configurations(dt: int):
+    for G in glv.SCORE_GROUPS[dt]:
+        for pipe in (False, True):
+            yield G, pipe
+
+
+def tune_score(index, Q, off, ids, kappa: int, reps: int = 5, use_cache: bool = True, verbose: bool = False):
+    """Pick the fastest scoring configuration for ``index``'s store on this workload.
+    Returns (G, pipelined, table) where table maps "G/pipe" to the mean ms per call."""
+    nq = Q.shape[0]
+    mean_len = ids.shape[0] / max(nq, 1)
+    key = _key(index.dt, index.d, index.C, mean_len)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        G, pipe = cache[key]["G"], cache[key]["pipe"]
+        glv.glv_set_score_config(index.dt, G, pipe)
+        return G, pipe, cache[key].get("table", {})
+    b = index._buffers(nq, ids.shape[0], kappa, kappa)
+    glv.glv_project_queries(Q, index.A, index.compute, Qp=b["Qp"], workspace=b["pws"])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=Q.device)  # 256 MB > L2
+    table = {}
+    seen = set()
+    for G, pipe in configurations(index.dt):
+        glv.glv_set_score_config(index.dt, G, pipe)
+        eff = glv.glv_get_score_config(index.dt, index.d)
+        if eff in seen:  # this choice cannot serve the row width; it maps onto one already timed
+            continue
+        seen.add(eff)
+
+        def run():
+            glv.glv_score_topk(b["Qp"], index.Xred, index.row_stride, index.scales, index.dt, index.tags, off,
+                               ids, kappa, scores_scratch=b["scores"], out_s=b["ts"], out_id=b["ti"])
+        run()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        table[f"{eff[0]}/{int(eff[1])}"] = ms / reps
+        if verbose:
+            print(f"  score config G={eff[0]:2d} pipe={int(eff[1])}: {ms / reps:.3f} ms", flush=True)
+    best = min(table, key=table.get)
+    G, pipe = (int(x) for x in best.split("/"))
+    glv.glv_set_score_config(index.dt, G, bool(pipe))
+    if use_cache:
+        cache[key] = {"G": G, "pipe": bool(pipe), "table": table}
+        _save_cache(cache)
+    return G, bool(pipe), table

@@ -47,7 +47,7 @@ static glv_status fill_score_args(ScoreArgs& a, const float* Qp, int64_t nq, int
   GLV_CHECK((size_t)C * (dpad + 4) * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
   const int64_t bytes = (int64_t)d * eb;
   const int nch = (int)((bytes + 15) / 16);
-  GLV_CHECK(nch <= 32 * 8, GLV_ERR_UNSUPPORTED);
+  GLV_CHECK(nch <= 32 * 10, GLV_ERR_UNSUPPORTED);
   a.Qp = Qp;
   a.C = C;
   a.d = d;
@@ -183,6 +183,22 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
   GLV_CHECK(out_s && out_id, GLV_ERR_INVALID_ARG);
   GLV_CHECK(fused_smem_bytes(C, d, dt) <= kSmemLimit - 12 * 1024, GLV_ERR_UNSUPPORTED);  // + static TopkSmem
   GLV_LAUNCH(launch_score_topk(a, dt, nq, kappa, out_s, out_id, num_sms(), (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t pipelined) {
+  GLV_CHECK(valid_dt(dt), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(set_score_config(dt, lanes_per_candidate, pipelined != 0), GLV_ERR_INVALID_ARG);
+  return GLV_OK;
+}
+
+glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate, int32_t* pipelined) {
+  GLV_CHECK(valid_dt(dt) && d >= 1 && lanes_per_candidate && pipelined, GLV_ERR_INVALID_ARG);
+  const int nch = (int)(((int64_t)d * elem_bytes(dt) + 15) / 16);
+  int G = 0, pipe = 0;
+  effective_score_config(dt, nch, &G, &pipe);
+  *lanes_per_candidate = G;
+  *pipelined = pipe;
   return GLV_OK;
 }
 

@@ -41,15 +41,20 @@ GLV_DEV float e4m3_hi_byte_scaled(uint32_t t) {
   return __uint_as_float((t & 0x80000000u) | ((t & 0x7f000000u) >> 4));
 }
 
+// Dot product of one 16-byte chunk of a reduced row with the matching projected-query
+// elements.  The projected query of a cluster is laid out in shared memory as EPC/4
+// sub-blocks of float4, each sub-block holding the same 4-element slice of every chunk:
+// element (chunk ch, e) sits at float4 index (e / 4) * nch + ch.  Lanes that read
+// consecutive chunks of one row then read consecutive float4 words (no bank conflicts).
 template <int DT>
-GLV_DEV float dot_chunk(uint4 v, const float* q) {
-  const float4* q4 = reinterpret_cast<const float4*>(q);
+GLV_DEV float dot_chunk(uint4 v, const float* qrow, int ch, int nch) {
+  const float4* q4 = reinterpret_cast<const float4*>(qrow);
   if constexpr (DT == GLV_F32) {
-    float4 a = q4[0];
+    float4 a = q4[ch];
     return a.x * __uint_as_float(v.x) + a.y * __uint_as_float(v.y) + a.z * __uint_as_float(v.z) +
            a.w * __uint_as_float(v.w);
   } else if constexpr (DT == GLV_BF16) {
-    float4 a = q4[0], b = q4[1];
+    float4 a = q4[ch], b = q4[nch + ch];
     float s = a.x * __uint_as_float(v.x << 16);
     s = fmaf(a.y, __uint_as_float(v.x & 0xffff0000u), s);
     s = fmaf(a.z, __uint_as_float(v.y << 16), s);
@@ -64,7 +69,7 @@ GLV_DEV float dot_chunk(uint4 v, const float* q) {
     float s = 0.f;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      float4 a = q4[t];
+      float4 a = q4[t * nch + ch];
       s = fmaf(a.x, e4m3_hi_byte_scaled(w[t] << 24), s);
       s = fmaf(a.y, e4m3_hi_byte_scaled(w[t] << 16), s);
       s = fmaf(a.z, e4m3_hi_byte_scaled(w[t] << 8), s);
@@ -88,76 +93,121 @@ GLV_DEV uint4 keep_bytes(uint4 v, int nbytes) {
 
 
 
-// Stage the C projected views of query j into shared memory, zero padded to a.qstride.
+// Stage the C projected views of query j into shared memory in the sub-block layout of
+// dot_chunk (rows of a.qstride floats; elements d..dpad-1 are zero).
+template <int DT>
 GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
+  constexpr int EPC = Elem<DT>::kPerChunk;
   const float* qj = a.Qp + j * (int64_t)a.C * a.d;
-  const int total = a.C * a.qstride;
+  const int dpad = a.nch * EPC;
+  const int total = a.C * dpad;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int c = t / a.qstride, r = t - c * a.qstride;
-    qs[t] = (r < a.d) ? qj[(int64_t)c * a.d + r] : 0.f;
+    const int c = t / dpad, r = t - c * dpad;
+    const int ch = r / EPC, e = r - ch * EPC;
+    qs[c * a.qstride + ((e >> 2) * a.nch + ch) * 4 + (e & 3)] = (r < a.d) ? qj[(int64_t)c * a.d + r] : 0.f;
   }
 }
 
 // Score candidates p in [b0, b1) with the CTA's warps; sink(p, score) receives each score
 // (from lane 0 of the candidate's lane group).  A bad id or tag scores -inf and is reported.
-template <int DT, int G, int NCH, class Sink>
+// PIPE: the row loads of the next candidate are issued before the current one is computed
+// (twice the registers for row data, a continuous stream of loads per warp).
+template <int DT, int G, int NCH, bool PIPE>
+struct RowLoad {
+  uint4 v[NCH];
+  int tag;
+  float sc;
+  bool ok, in;
+  int64_t p;
+};
+
+template <int DT, int G, int NCH, bool PIPE>
+GLV_DEV void load_row(const ScoreArgs& a, RowLoad<DT, G, NCH, PIPE>& r, int64_t p, int64_t b1, int64_t id,
+                      int gl) {
+  r.p = p;
+  r.in = p < b1;
+  r.ok = r.in && id >= 0 && id < a.N;
+  r.tag = r.ok ? (int)__ldg(a.tags + id) : 0;
+  const uint8_t* row = a.Xred + id * a.row_stride;
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    const int ch = gl + t * G;
+    r.v[t] = (r.ok && ch < a.nch) ? ld_stream_v4(row + (int64_t)ch * 16) : make_uint4(0, 0, 0, 0);
+  }
+  r.sc = 1.f;
+  if constexpr (DT == GLV_FP8_E4M3) r.sc = r.ok ? __ldg(a.scales + id) : 0.f;
+}
+
+template <int DT, int G, int NCH, bool PIPE, class Sink>
+GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, const float* qs, int gl,
+                        Sink& sink) {
+  const bool ok = r.ok && r.tag < a.C;
+  const float* qrow = qs + (ok ? r.tag : 0) * a.qstride;
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    const int ch = gl + t * G;
+    if (ch < a.nch) {
+      uint4 x = r.v[t];
+      if (ch == a.nch - 1 && a.tail < 16) x = keep_bytes(x, a.tail);
+      acc += dot_chunk<DT>(x, qrow, ch, a.nch);
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (r.in && gl == 0) {
+    float s;
+    if (!ok) {
+      s = -INFINITY;
+      report(a.d_status, GLV_ERR_BAD_ID);
+    } else if constexpr (DT == GLV_FP8_E4M3) {
+      s = (acc * 0x1p120f) * r.sc;
+    } else {
+      s = acc;
+    }
+    sink(r.p, s);
+  }
+}
+
+template <int DT, int G, int NCH, bool PIPE, class Sink>
 GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_t b1, Sink sink) {
-  constexpr int EPC = Elem<DT>::kPerChunk;
   constexpr int GPW = kWarp / G;
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int g = lane / G, gl = lane % G;
-
   const int64_t step = (int64_t)nwarps * GPW;
   int64_t base = b0 + (int64_t)warp * GPW;
   // the id of the next candidate is loaded one iteration ahead, so the row loads of an
   // iteration do not wait for an id round trip
   int64_t id_next = (base + g < b1) ? (int64_t)__ldg(a.ids + base + g) : 0;
-  for (; base < b1; base += step) {
-    const int64_t p = base + g;
-    const bool in = p < b1;
-    const int64_t id = id_next;
-    id_next = (p + step < b1) ? (int64_t)__ldg(a.ids + p + step) : 0;
-    bool ok = in && id >= 0 && id < a.N;
-    int tag = ok ? (int)__ldg(a.tags + id) : 0;
-    if (ok && tag >= a.C) ok = false;
-
-    uint4 v[NCH];
-    const uint8_t* row = a.Xred + id * a.row_stride;
-#pragma unroll
-    for (int t = 0; t < NCH; ++t) {
-      const int ch = gl + t * G;
-      v[t] = (ok && ch < a.nch) ? ld_stream_v4(row + (int64_t)ch * 16) : make_uint4(0, 0, 0, 0);
+  if constexpr (!PIPE) {
+    for (; base < b1; base += step) {
+      const int64_t p = base + g;
+      const int64_t id = id_next;
+      id_next = (p + step < b1) ? (int64_t)__ldg(a.ids + p + step) : 0;
+      RowLoad<DT, G, NCH, PIPE> r;
+      load_row(a, r, p, b1, id, gl);
+      finish_row(a, r, qs, gl, sink);
     }
-    float sc = 1.f;
-    if constexpr (DT == GLV_FP8_E4M3) sc = ok ? __ldg(a.scales + id) : 0.f;
-
-    float acc = 0.f;
-    const float* qrow = qs + tag * a.qstride;
-#pragma unroll
-    for (int t = 0; t < NCH; ++t) {
-      const int ch = gl + t * G;
-      if (ch < a.nch) {
-        uint4 x = v[t];
-        if (ch == a.nch - 1 && a.tail < 16) x = keep_bytes(x, a.tail);
-        acc += dot_chunk<DT>(x, qrow + ch * EPC);
-      }
+  } else {
+    if (base >= b1) return;
+    RowLoad<DT, G, NCH, PIPE> cur, nxt;
+    {
+      const int64_t p = base + g;
+      const int64_t id = id_next;
+      id_next = (p + step < b1) ? (int64_t)__ldg(a.ids + p + step) : 0;
+      load_row(a, cur, p, b1, id, gl);
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-
-    if (in && gl == 0) {
-      float s;
-      if (!ok) {
-        s = -INFINITY;
-        report(a.d_status, GLV_ERR_BAD_ID);
-      } else if constexpr (DT == GLV_FP8_E4M3) {
-        s = (acc * 0x1p120f) * sc;
-      } else {
-        s = acc;
+    for (; base < b1; base += step) {
+      const int64_t pn = base + step + g;
+      if (base + step < b1) {
+        const int64_t id = id_next;
+        id_next = (pn + step < b1) ? (int64_t)__ldg(a.ids + pn + step) : 0;
+        load_row(a, nxt, pn, b1, id, gl);
       }
-      sink(p, s);
+      finish_row(a, cur, qs, gl, sink);
+      cur = nxt;
     }
   }
 }

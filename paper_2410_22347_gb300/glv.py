@@ -48,6 +48,8 @@ def _load() -> ctypes.CDLL:
         "glv_score_candidates": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P]),
         "glv_score_topk": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, i32, P, P, P, P, P]),
         "glv_topk": (i32, [P, P, P, i64, i32, P, P, P]),
+        "glv_set_score_config": (i32, [i32, i32, i32]),
+        "glv_get_score_config": (i32, [i32, i32, P, P]),
         "glv_rerank": (i32, [P, i64, i32, P, i64, P, i32, i32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -223,6 +225,20 @@ def glv_score_topk(Qp, Xred, row_stride: int, scales, dt: int, tags, off, ids, k
                                _ptr(off), _ptr(ids), kappa, _ptr(scores_scratch), _ptr(out_s), _ptr(out_id),
                                _ptr(d_status), _stream(stream)))
     return out_s, out_id
+
+
+SCORE_GROUPS = {GLV_F32: (4, 8, 16, 32), GLV_BF16: (2, 4, 8, 32), GLV_FP8_E4M3: (1, 2, 4, 32)}
+
+
+def glv_set_score_config(dt: int, lanes_per_candidate: int, pipelined: bool) -> None:
+    _check("glv_set_score_config", _lib.glv_set_score_config(dt, int(lanes_per_candidate), int(bool(pipelined))))
+
+
+def glv_get_score_config(dt: int, d: int) -> tuple[int, bool]:
+    g = ctypes.c_int32(0)
+    p = ctypes.c_int32(0)
+    _check("glv_get_score_config", _lib.glv_get_score_config(dt, int(d), ctypes.byref(g), ctypes.byref(p)))
+    return int(g.value), bool(p.value)
 
 
 def glv_topk(scores, off, ids, kappa: int, out_s=None, out_id=None, stream=None):

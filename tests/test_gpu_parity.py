@@ -479,3 +479,33 @@ def test_index_search_matches_oracle(glv):
     hs, hi = ix.search_host(w.Q.pin_memory(), w.off.pin_memory(), w.ids.pin_memory(), w.kappa, w.k)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(hi.numpy(), fi)
+
+
+# ---------------------------------------------------------------------------------------
+# every scoring configuration the autotuner may pick stays exact
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
+def test_every_score_configuration_matches_oracle(glv, dt_name):
+    dt = glv.DTYPES[dt_name]
+    try:
+        for G in glv.SCORE_GROUPS[dt]:
+            for pipe in (False, True):
+                glv.glv_set_score_config(dt, G, pipe)
+                for d in (27, 160):
+                    _score_case(glv, dt, 300 + G + d, d, 5, [0, 1, 700, 33, 2100, 1500], N=2500, D=max(d, 64))
+    finally:
+        glv.glv_set_score_config(dt, 0, False)
+
+
+def test_score_config_roundtrip(glv):
+    try:
+        glv.glv_set_score_config(glv.GLV_BF16, 8, True)
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, True)
+        # 8 lanes x 5 pipelined loads cannot cover a 160-chunk row: falls back to a default
+        g, p = glv.glv_get_score_config(glv.GLV_BF16, 1280)
+        assert not p
+        with pytest.raises(glv.GlvError):
+            glv.glv_set_score_config(glv.GLV_BF16, 3, False)
+    finally:
+        glv.glv_set_score_config(glv.GLV_BF16, 0, False)
