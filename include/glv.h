@@ -228,6 +228,57 @@ glv_status glv_rerank(const float* X, int64_t N, int32_t D, const float* Q, int6
                       const int32_t* surv_id, int32_t kappa, int32_t k, float* out_s,
                       int32_t* out_id, int32_t* d_status, void* stream);
 
+/* =======================================================================================
+ * Learning side: statistics of LeanVec-Sphering and the gradient used to refine it.
+ * ===================================================================================== */
+
+/* ---------------------------------------------------------------------------------------
+ * Second moments K = sum_v v v^T (the D x D summary statistics of Section 3.2, from which
+ * Algorithm 2 is computed by eigendecompositions: K_Q for the queries, K_{X_c} for the
+ * database vectors of each cluster, Algorithm 5).  FP32 inputs, FP64 products and sums.
+ *   V    : n x D float32.
+ *   tags : n uint16 cluster of each vector, or NULL (then C must be 1: one matrix over all).
+ *   K    : C x D x D float64 output (row-major, symmetric; clusters with no vector get 0).
+ *   workspace : glv_second_moments_workspace_size(n, C) bytes (256-aligned) when tags are
+ *               given, else may be NULL.   d_status : tag >= C -> GLV_ERR_BAD_ID, skipped.
+ * ------------------------------------------------------------------------------------- */
+size_t glv_second_moments_workspace_size(int64_t n, int32_t C);
+glv_status glv_second_moments(const float* V, int64_t n, int32_t D, const uint16_t* tags,
+                              int32_t C, double* K, void* workspace, int32_t* d_status,
+                              void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Pair forward of the inner-product approximation loss (the LeanVec problem of Section 2.1
+ * restricted to GleanVec pairs, Section 4.1): for P index pairs p = (qi[p], xi[p]) with
+ * cluster c = tags[xi[p]],
+ *     u_p = B_c x_p,  v_p = A_c q_p  (d each),  s_p = <u_p, v_p>,  t_p = <q_p, x_p>.
+ * The loss sum_p (t_p - s_p)^2 and its gradient follow from s, t (see glv_pair_backward).
+ *   Q : nQ x D, X : nX x D float32;  A, B : C x d x D float32;  qi, xi : P int32.
+ *   s, t : P float32 outputs;  u, v : P x d float32 outputs (kept for the backward).
+ *   workspace : glv_pair_workspace_size(P, C) bytes, 256-aligned.
+ *   A pair with an index or tag out of range gets s = t = 0, u = v = 0 and GLV_ERR_BAD_ID.
+ * ------------------------------------------------------------------------------------- */
+size_t glv_pair_workspace_size(int64_t P, int32_t C);
+glv_status glv_pair_forward(const float* Q, int64_t nQ, const float* X, int64_t nX, int32_t D,
+                            const uint16_t* tags, const float* A, const float* B, int32_t C,
+                            int32_t d, const int32_t* qi, const int32_t* xi, int64_t P, float* s,
+                            float* t, float* u, float* v, void* workspace, int32_t* d_status,
+                            void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Pair backward (the gather-score backward): given g_p = dL/ds_p,
+ *     dA_c = sum_{p: c_p = c} g_p u_p q_p^T,    dB_c = sum_{p: c_p = c} g_p v_p x_p^T,
+ * a segmented sum of rank-1 terms per cluster (pairs grouped by cluster on the device, one
+ * FP32 GEMM over each cluster's pairs).  For L = sum_p (t_p - s_p)^2, g_p = -2 (t_p - s_p).
+ *   u, v : from glv_pair_forward on the same pairs;  g : P float32.
+ *   dA, dB : C x d x D float32 outputs (overwritten; clusters without pairs get 0).
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_pair_backward(const float* Q, int64_t nQ, const float* X, int64_t nX, int32_t D,
+                             const uint16_t* tags, int32_t C, int32_t d, const int32_t* qi,
+                             const int32_t* xi, int64_t P, const float* u, const float* v,
+                             const float* g, float* dA, float* dB, void* workspace,
+                             int32_t* d_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -238,4 +238,62 @@ glv_status glv_rerank(const float* X, int64_t N, int32_t D, const float* Q, int6
   return GLV_OK;
 }
 
+size_t glv_second_moments_workspace_size(int64_t n, int32_t C) {
+  if (n < 0 || C < 1) return 0;
+  return moments_ws_bytes(n, C);
+}
+
+glv_status glv_second_moments(const float* V, int64_t n, int32_t D, const uint16_t* tags, int32_t C, double* K,
+                              void* workspace, int32_t* d_status, void* stream) {
+  GLV_CHECK(n >= 0 && n <= 2147483647LL && D >= 1 && C >= 1 && C <= 65535, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(tags != nullptr || C == 1, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(V || n == 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(K != nullptr, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(tags == nullptr || (workspace && aligned(workspace, 256)), GLV_ERR_INVALID_ARG);
+  const int nt = (D + 63) / 64;
+  GLV_CHECK((int64_t)nt * (nt + 1) / 2 <= kMaxGridX, GLV_ERR_UNSUPPORTED);
+  GLV_LAUNCH(launch_moments(V, n, D, tags, C, K, workspace, d_status, (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+size_t glv_pair_workspace_size(int64_t P, int32_t C) {
+  if (P < 0 || C < 1) return 0;
+  return pair_ws_bytes(P, C);
+}
+
+glv_status glv_pair_forward(const float* Q, int64_t nQ, const float* X, int64_t nX, int32_t D,
+                            const uint16_t* tags, const float* A, const float* B, int32_t C, int32_t d,
+                            const int32_t* qi, const int32_t* xi, int64_t P, float* s, float* t, float* u,
+                            float* v, void* workspace, int32_t* d_status, void* stream) {
+  GLV_CHECK(nQ >= 0 && nX >= 0 && D >= 1 && C >= 1 && C <= 65535 && d >= 1 && d <= D && P >= 0,
+            GLV_ERR_INVALID_ARG);
+  GLV_CHECK(P <= 2147483647LL, GLV_ERR_UNSUPPORTED);
+  if (P == 0) return GLV_OK;
+  GLV_CHECK(Q && X && tags && A && B && qi && xi && s && t && u && v && workspace, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(aligned(workspace, 256), GLV_ERR_INVALID_ARG);
+  GLV_LAUNCH(launch_pair_forward(Q, nQ, X, nX, D, tags, A, B, C, d, qi, xi, P, s, t, u, v, workspace, d_status,
+                                 (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_pair_backward(const float* Q, int64_t nQ, const float* X, int64_t nX, int32_t D,
+                             const uint16_t* tags, int32_t C, int32_t d, const int32_t* qi, const int32_t* xi,
+                             int64_t P, const float* u, const float* v, const float* g, float* dA, float* dB,
+                             void* workspace, int32_t* d_status, void* stream) {
+  GLV_CHECK(nQ >= 0 && nX >= 0 && D >= 1 && C >= 1 && C <= 65535 && d >= 1 && d <= D && P >= 0,
+            GLV_ERR_INVALID_ARG);
+  GLV_CHECK(P <= 2147483647LL, GLV_ERR_UNSUPPORTED);
+  GLV_CHECK(dA && dB, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(P == 0 || (Q && X && tags && qi && xi && u && v && g && workspace && aligned(workspace, 256)),
+            GLV_ERR_INVALID_ARG);
+  if (P == 0) {  // no pairs: zero gradient
+    GLV_LAUNCH(cudaMemsetAsync(dA, 0, sizeof(float) * (size_t)C * d * D, (cudaStream_t)stream));
+    GLV_LAUNCH(cudaMemsetAsync(dB, 0, sizeof(float) * (size_t)C * d * D, (cudaStream_t)stream));
+    return GLV_OK;
+  }
+  GLV_LAUNCH(launch_pair_backward(Q, nQ, X, nX, D, tags, C, d, qi, xi, P, u, v, g, dA, dB, workspace, d_status,
+                                  (cudaStream_t)stream));
+  return GLV_OK;
+}
+
 }  // extern "C"

@@ -19,14 +19,6 @@ constexpr int kBuildTM = 32;   // rows per tile
 constexpr int kBuildTN = 64;   // output columns per pass
 constexpr int kBuildBK = 32;   // K slice
 
-struct BuildWs {
-  int32_t* counts;      // C
-  int32_t* cursor;      // C
-  int32_t* seg_start;   // C
-  int32_t* tile_start;  // C + 1 (last = number of tiles)
-  int32_t* perm;        // N
-};
-
 static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 size_t build_ws_bytes(int64_t N, int C) {
@@ -276,17 +268,23 @@ __global__ void __launch_bounds__(256) build_gemm_kernel(const BuildArgs a) {
   }
 }
 
-cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags, const float* B,
-                         int C, int d, int dt, void* Xred, int64_t row_stride, float* scales,
-                         void* workspace, int32_t* d_status, cudaStream_t st) {
-  BuildWs ws = build_ws_carve(workspace, N, C);
+cudaError_t launch_grouping(const uint16_t* tags, int64_t N, int C, const BuildWs& ws, int32_t* d_status,
+                            cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ws.counts, 0, 8 * (size_t)C, st);  // counts + cursor
   if (e != cudaSuccess) return e;
   const int hb = (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096);
   build_hist_kernel<<<hb, 256, 0, st>>>(tags, N, C, ws.counts, d_status);
   build_scan_kernel<<<1, 1024, 0, st>>>(ws.counts, C, ws.seg_start, ws.tile_start);
   build_scatter_kernel<<<hb, 256, 0, st>>>(tags, N, C, ws.seg_start, ws.cursor, ws.perm);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags, const float* B,
+                         int C, int d, int dt, void* Xred, int64_t row_stride, float* scales,
+                         void* workspace, int32_t* d_status, cudaStream_t st) {
+  BuildWs ws = build_ws_carve(workspace, N, C);
+  cudaError_t e = launch_grouping(tags, N, C, ws, d_status, st);
+  if (e != cudaSuccess) return e;
 
   BuildArgs a;
   a.X = X; a.N = N; a.D = D; a.B = B; a.C = C; a.d = d;

@@ -50,7 +50,31 @@ cudaError_t launch_project_simt(const float* Q, int64_t nq, int D, const float* 
 size_t project_tc_ws_bytes(int64_t nq, int D, int64_t Mc, int bf16);
 cudaError_t launch_project_tc(const float* Q, int64_t nq, int D, const float* A, int64_t Mc, float* Qp,
                               int bf16, void* ws, int32_t* d_status, int num_sms, cudaStream_t st);
+// Rows grouped by cluster: counts[c], seg_start[c] (exclusive scan), tile_start[c] (32-row
+// tiles), and perm = row ids ordered by cluster (within a cluster in arbitrary order).
+struct BuildWs {
+  int32_t* counts;      // C
+  int32_t* cursor;      // C
+  int32_t* seg_start;   // C
+  int32_t* tile_start;  // C + 1 (last = number of tiles)
+  int32_t* perm;        // N
+};
+BuildWs build_ws_carve(void* ws, int64_t N, int C);
+cudaError_t launch_grouping(const uint16_t* tags, int64_t N, int C, const BuildWs& ws, int32_t* d_status,
+                            cudaStream_t st);
 size_t build_ws_bytes(int64_t N, int C);
+size_t moments_ws_bytes(int64_t n, int C);
+cudaError_t launch_moments(const float* V, int64_t n, int D, const uint16_t* tags, int C, double* K, void* ws,
+                           int32_t* d_status, cudaStream_t st);
+size_t pair_ws_bytes(int64_t P, int C);
+cudaError_t launch_pair_forward(const float* Q, int64_t nQ, const float* X, int64_t nX, int D, const uint16_t* tags,
+                                const float* A, const float* B, int C, int d, const int32_t* qi, const int32_t* xi,
+                                int64_t P, float* s, float* t, float* u, float* v, void* ws, int32_t* d_status,
+                                cudaStream_t st);
+cudaError_t launch_pair_backward(const float* Q, int64_t nQ, const float* X, int64_t nX, int D,
+                                 const uint16_t* tags, int C, int d, const int32_t* qi, const int32_t* xi, int64_t P,
+                                 const float* u, const float* v, const float* g, float* dA, float* dB, void* ws,
+                                 int32_t* d_status, cudaStream_t st);
 cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags, const float* B,
                          int C, int d, int dt, void* Xred, int64_t row_stride, float* scales,
                          void* workspace, int32_t* d_status, cudaStream_t st);

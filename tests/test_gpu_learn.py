@@ -1,0 +1,140 @@
+"""GPU parity of the learning side: FP64 second moments, the per-cluster LeanVec-Sphering
+initialisation, the pair forward and the hand-written backward (against the FP64 oracle
+gradient and central finite differences), and that refinement lowers the loss."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def learn():
+    from paper_2410_22347_gb300 import build_lib
+    build_lib.build()
+    from paper_2410_22347_gb300 import learn as L
+    return L
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def _sets(seed, D, nq, nx, C):
+    rng = np.random.default_rng(seed)
+    sq = np.arange(1, D + 1) ** -0.25
+    sx = np.arange(1, D + 1) ** -0.5
+    Rq = np.linalg.qr(rng.standard_normal((D, D)))[0]
+    Rx = np.linalg.qr(rng.standard_normal((D, D)))[0]
+    Q = ((rng.standard_normal((nq, D)) * sq) @ Rq.T).astype(np.float32)
+    X = ((rng.standard_normal((nx, D)) * sx) @ Rx.T).astype(np.float32)
+    mu = X[rng.choice(nx, C, replace=False)]
+    return rng, Q, X, mu
+
+
+@pytest.mark.parametrize("n,D,C", [(1000, 64, 1), (3000, 100, 5), (777, 33, 3), (5000, 256, 16)])
+def test_second_moments(learn, n, D, C):
+    rng, Q, X, mu = _sets(n + D, D, 10, n, max(C, 1))
+    tags = oracle.assign_tags(X, mu) if C > 1 else None
+    K = learn.glv_second_moments(_t(X), None if tags is None else _t(tags), C).cpu().numpy()
+    for c in range(C):
+        ref = oracle.second_moment(X, tags, c if tags is not None else -1)
+        np.testing.assert_allclose(K[c], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_sphering_init_matches_oracle(learn):
+    D, d, C = 48, 12, 4
+    rng, Q, X, mu = _sets(5, D, 400, 3000, C)
+    tags = oracle.assign_tags(X, mu)
+    A, B = learn.sphering_init(_t(Q), _t(X), _t(tags), C, d)
+    Ar, Br = oracle.gleanvec_sphering(Q, X, tags, C, d)
+    A, B = A.cpu().numpy().astype(np.float64), B.cpu().numpy().astype(np.float64)
+    for c in range(C):
+        # eigenvector signs are arbitrary; A_c^T B_c (the reduction's bilinear form) is not
+        np.testing.assert_allclose(A[c].T @ B[c], Ar[c].T @ Br[c], atol=2e-5)
+    # and the loss each cluster reaches equals the oracle's
+    qi, xi = np.meshgrid(np.arange(400), np.arange(3000), indexing="ij")
+    sel = np.random.default_rng(1).choice(qi.size, 20000, replace=False)
+    l_gpu = oracle.pair_loss_grad(Q, X, tags, A.astype(np.float32), B.astype(np.float32), qi.ravel()[sel],
+                                  xi.ravel()[sel], want_grad=False)
+    l_ref = oracle.pair_loss_grad(Q, X, tags, Ar.astype(np.float32), Br.astype(np.float32), qi.ravel()[sel],
+                                  xi.ravel()[sel], want_grad=False)
+    assert abs(l_gpu - l_ref) <= 1e-4 * l_ref
+
+
+@pytest.mark.parametrize("D,d,C,P", [(64, 16, 3, 500), (128, 32, 16, 4096), (100, 27, 5, 1000)])
+def test_pair_forward_and_backward_vs_oracle(learn, D, d, C, P):
+    rng, Q, X, mu = _sets(D + P, D, 300, 2000, C)
+    tags = oracle.assign_tags(X, mu)
+    A = (rng.standard_normal((C, d, D)) / np.sqrt(D)).astype(np.float32)
+    B = (rng.standard_normal((C, d, D)) / np.sqrt(D)).astype(np.float32)
+    qi = rng.integers(0, 300, P).astype(np.int32)
+    xi = rng.integers(0, 2000, P).astype(np.int32)
+    st = torch.zeros(1, dtype=torch.int32, device=dev())
+    s, t, u, v = learn.glv_pair_forward(_t(Q), _t(X), _t(tags), _t(A), _t(B), _t(qi), _t(xi), d_status=st)
+    assert st.item() == 0
+    # forward against the oracle's reduced rows and projections
+    Xr = oracle.build_reduced(X, tags, B)
+    Qp = oracle.project(Q, A)
+    s_ref = np.einsum("pr,pr->p", Xr[xi], Qp[qi, tags[xi]])
+    t_ref = np.einsum("pk,pk->p", Q[qi].astype(np.float64), X[xi].astype(np.float64))
+    scale = np.linalg.norm(Xr[xi], axis=1) * np.linalg.norm(Qp[qi, tags[xi]], axis=1)
+    assert np.all(np.abs(s.cpu().numpy() - s_ref) <= 1e-5 * np.maximum(np.abs(s_ref), scale))
+    assert np.all(np.abs(t.cpu().numpy() - t_ref) <= 1e-5 * np.linalg.norm(Q[qi], axis=1) * np.linalg.norm(X[xi], axis=1))
+    # backward of L = sum (t - s)^2: g = -2 (t - s)
+    g = -2.0 * (t - s)
+    dA, dB = learn.glv_pair_backward(_t(Q), _t(X), _t(tags), C, _t(qi), _t(xi), u, v, g)
+    loss, gA, gB = oracle.pair_loss_grad(Q, X, tags, A, B, qi, xi)
+    for got, ref in ((dA.cpu().numpy(), gA), (dB.cpu().numpy(), gB)):
+        err = np.abs(got - ref).max()
+        assert err <= 1e-4 * np.abs(ref).max(), (err, np.abs(ref).max())
+
+
+def test_autograd_matches_finite_differences(learn):
+    """Central differences (step 1e-3) of the FP32 forward against the backward kernel."""
+    D, d, C, P = 64, 16, 3, 2048
+    rng, Q, X, mu = _sets(9, D, 200, 1500, C)
+    tags = _t(oracle.assign_tags(X, mu))
+    A = _t((rng.standard_normal((C, d, D)) / np.sqrt(D)).astype(np.float32)).requires_grad_(True)
+    B = _t((rng.standard_normal((C, d, D)) / np.sqrt(D)).astype(np.float32)).requires_grad_(True)
+    qi = _t(rng.integers(0, 200, P).astype(np.int32))
+    xi = _t(rng.integers(0, 1500, P).astype(np.int32))
+    Qt, Xt = _t(Q), _t(X)
+    loss = learn.pair_loss(A, B, Qt, Xt, tags, qi, xi)
+    loss.backward()
+    h = 1e-3
+    for which, M, G in (("A", A, A.grad), ("B", B, B.grad)):
+        for (c, r, k) in [(0, 0, 0), (1, 5, 17), (2, 15, 63), (1, 3, 40)]:
+            with torch.no_grad():
+                base = M[c, r, k].item()
+                M[c, r, k] = base + h
+                lp = learn.pair_loss(A, B, Qt, Xt, tags, qi, xi).double().item()
+                M[c, r, k] = base - h
+                lm = learn.pair_loss(A, B, Qt, Xt, tags, qi, xi).double().item()
+                M[c, r, k] = base
+            fd = (lp - lm) / (2 * h)
+            gv = G[c, r, k].item()
+            # FP32 loss evaluations: absolute noise ~ 1e-7 * loss / h
+            assert abs(fd - gv) <= 1e-3 * max(abs(gv), 1.0) + 2e-7 * loss.item() / h, (which, c, r, k, fd, gv)
+
+
+def test_refine_lowers_loss_from_sphering_init(learn):
+    D, d, C = 64, 8, 4
+    rng, Q, X, mu = _sets(13, D, 2000, 8000, C)
+    tags_np = oracle.assign_tags(X, mu)
+    Qt, Xt, tags = _t(Q), _t(X), _t(tags_np)
+    A0, B0 = learn.sphering_init(Qt, Xt, tags, C, d)
+    qi, xi = (torch.from_numpy(rng.integers(0, n, 20000).astype(np.int32)).to(dev()) for n in (2000, 8000))
+    with torch.no_grad():
+        l0 = learn.pair_loss(A0, B0, Qt, Xt, tags, qi, xi).item()
+    A1, B1, hist = learn.refine(A0, B0, Qt, Xt, tags, steps=150, batch=4096, lr=2e-3, seed=3)
+    with torch.no_grad():
+        l1 = learn.pair_loss(A1, B1, Qt, Xt, tags, qi, xi).item()
+    assert np.isfinite(hist).all()
+    assert l1 < l0
