@@ -49,6 +49,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-queries-per-step", type=int, default=256)
     p.add_argument("--no-autotune", action="store_true", help="keep the library's default scoring configuration")
+    p.add_argument("--graph", action="store_true", help="time the step as a captured CUDA graph")
+    p.add_argument("--queries", default="ood", choices=["ood", "id"], help="query distribution")
+    p.add_argument("--score-error", action="store_true",
+                   help="report each store's score error against the FP64 oracle on the recall sample")
+    p.add_argument("--per-query", type=int, default=0,
+                   help="also time the per-query launch path on this many queries (batching comparison)")
     p.add_argument("--override", nargs="*", default=[],
                    help="workload fields to override, e.g. nq=2000 D=256 (smaller profiling cases)")
     a = p.parse_args()
@@ -241,7 +247,7 @@ def run_reference(args):
     from paper_2410_22347_gb300 import synth
 
     oracle.set_threads(os.cpu_count() or 1)
-    w = synth.workload(args.workload, device="cpu", **args.overrides)
+    w = synth.workload(args.workload, device="cpu", queries=args.queries, **args.overrides)
     X, Q, mu, A, B = (t.numpy() for t in (w.X, w.Q, w.mu, w.A, w.B))
     off, ids = w.off.numpy(), w.ids.numpy()
     nq = Q.shape[0]
@@ -303,7 +309,7 @@ def run_glv(args):
     from paper_2410_22347_gb300 import glv, synth
     from paper_2410_22347_gb300.index import GleanVecIndex
 
-    w = synth.workload(args.workload, device=dev, replica=rank, **args.overrides)
+    w = synth.workload(args.workload, device=dev, replica=rank, queries=args.queries, **args.overrides)
     nq, D = w.Q.shape
     C, d, _ = w.A.shape
     total = int(w.off[-1])
@@ -340,8 +346,8 @@ def run_glv(args):
         ix = idx[st]
         if not args.no_autotune:  # untimed set-up: pick the scoring configuration for this store
             from paper_2410_22347_gb300.autotune import tune_score
-            G, pipe, table = tune_score(ix, w.Q, w.off, w.ids, w.kappa, use_cache=False)
-            tuned[st] = {"lanes_per_candidate": G, "pipelined": pipe, "ms_by_config": table}
+            G, mode, table = tune_score(ix, w.Q, w.off, w.ids, w.kappa, use_cache=False)
+            tuned[st] = {"lanes_per_candidate": G, "gather_mode": mode, "ms_by_config(G/mode)": table}
         for _ in range(args.warmup):
             step(ix)
         torch.cuda.synchronize()
@@ -372,6 +378,69 @@ def run_glv(args):
                            kernels_ms={n: statistics.mean(v) for n, v in
                                        zip(("project", "score_topk", "rerank"), kern)},
                            wall_s=wall)
+
+    # ---- batching: the step as one CUDA graph, and the per-query launch path ----
+    batching = {}
+    if args.graph or args.per_query:
+        ix = idx[args.store]
+        if args.graph:
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                step(ix)  # warm the buffers on the capture stream
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
+                step(ix)
+            g.replay()
+            torch.cuda.synchronize()
+            gms = []
+            for _ in range(max(5, min(args.steps, 50))):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.replay()
+                e1.record()
+                e1.synchronize()
+                gms.append(e0.elapsed_time(e1))
+            gms_max = max_over_ranks(sum(gms) / len(gms))
+            batching["graph"] = {"ms_per_step": gms_max, "value": job_throughput(nq, world, gms_max)}
+        if args.per_query:
+            nsub = min(args.per_query, nq)
+            b = ix._buffers(nq, total, w.kappa, w.k)
+            fsz, isz = 4, 4
+            Qp1 = torch.empty(1, C, d, dtype=torch.float32, device=dev)
+            pws1 = torch.empty(max(glv.project_workspace_bytes(1, D, C, d, ix.compute), 1), dtype=torch.uint8,
+                               device=dev)
+            lib = glv.lib()
+            stv = glv._stream(None)
+
+            def one(j):
+                # every query on its own: projection, scoring + top-kappa, re-rank (pointer offsets)
+                lib.glv_project_queries(w.Q.data_ptr() + j * D * 4, 1, D, ix.A.data_ptr(), C, d, ix.compute,
+                                        Qp1.data_ptr(), pws1.data_ptr(), None, stv)
+                lib.glv_score_topk(Qp1.data_ptr(), 1, C, d, ix.Xred.data_ptr(), ix.row_stride,
+                                   None if ix.scales is None else ix.scales.data_ptr(), ix.dt, ix.tags.data_ptr(),
+                                   ix.N, w.off.data_ptr() + j * 8, w.ids.data_ptr(), w.kappa,
+                                   b["scores"].data_ptr(), b["ts"].data_ptr() + j * w.kappa * fsz,
+                                   b["ti"].data_ptr() + j * w.kappa * isz, None, stv)
+                lib.glv_rerank(w.X.data_ptr(), ix.N, D, w.Q.data_ptr() + j * D * 4, 1,
+                               b["ti"].data_ptr() + j * w.kappa * isz, w.kappa, w.k,
+                               b["fs"].data_ptr() + j * w.k * fsz, b["fi"].data_ptr() + j * w.k * isz, None, stv)
+            for j in range(min(8, nsub)):
+                one(j)
+            torch.cuda.synchronize()
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for j in range(nsub):
+                one(j)
+            e1.record()
+            e1.synchronize()
+            pms = max_over_ranks(e0.elapsed_time(e1))
+            batching["per_query_launches"] = {"queries": nsub, "ms": pms,
+                                              "value": job_throughput(nsub, world, pms)}
 
     # ---- end-to-end through the public host API (pinned host buffers, copies timed) ----
     ix = idx[args.store]
@@ -417,6 +486,31 @@ def run_glv(args):
             torch.cuda.synchronize()
             recall[st] = oracle.recall(fi.cpu().numpy()[qsel], oid)
         line_extra["recall_10at10_vs_oracle"] = recall
+        if args.score_error:
+            # reduced-space scores of the sample, each store against the unquantised FP64 oracle
+            # (rows whose GPU tag differs from the oracle's near-tie decision are left out)
+            import oracle as orc
+            red, _ = orc.score(orc.project(sp["Q"], sp["A"]), sp["Xr"], sp["tags"], sp["off"], sp["ids"])
+            gtags = idx[args.store].tags.cpu().numpy()
+            rows = sp["uniq"][sp["ids"]]
+            same = gtags[rows] == sp["tags"][sp["ids"]]
+            qn = np.linalg.norm(orc.project(sp["Q"], sp["A"]), axis=2)
+            xn = np.linalg.norm(sp["Xr"], axis=1)
+            cj = np.repeat(np.arange(len(qsel)), np.diff(sp["off"]))
+            scale = np.maximum(np.abs(red), qn[cj, sp["tags"][sp["ids"]]] * xn[sp["ids"]])
+            errs = {}
+            for st in stores:
+                ix = idx[st]
+                b = ix._buffers(nq, total, w.kappa, w.k)
+                glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"])
+                sc = glv.glv_score_candidates(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off,
+                                              w.ids)
+                allsc = sc.cpu().numpy()
+                got = np.concatenate([allsc[offn[j]:offn[j + 1]] for j in qsel])
+                rel = np.abs(got - red)[same] / scale[same]
+                errs[st] = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
+                            "p99_rel": float(np.quantile(rel, 0.99))}
+            line_extra["score_error_vs_fp64_oracle"] = errs
         line_extra["recall_sample"] = f"{len(qsel)} random queries; oracle restricted to the rows they touch"
         if not args.no_cpu_baseline:
             csel = qsel if args.cpu_sample == len(qsel) else np.sort(
@@ -472,6 +566,7 @@ def run_glv(args):
         "modes": {st: {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernels_ms": r["kernels_ms"]}
                   for st, r in results.items()},
         "autotune": tuned or None,
+        "batching": batching or None,
     }
     line.update(line_extra)
     if rec is not None and rec < 0.9:
@@ -482,10 +577,103 @@ def run_glv(args):
     return 0
 
 
+def run_learn(args):
+    """Differentiation workload: 200k database + 20k OOD learning queries, D = 768, d = 128,
+    C = 16.  Times the FP64 second moments, the LeanVec-Sphering initialisation (host
+    eigendecompositions) and refinement minibatches of 4096 pairs (forward + backward +
+    Adam), and checks one minibatch gradient against the FP64 oracle."""
+    import numpy as np
+    import torch
+    from paper_2410_22347_gb300 import build_lib
+    build_lib.build()
+    from paper_2410_22347_gb300 import glv, learn, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    kw = dict(N=200_000, D=768, d=128, C=16, nq=20_000, K_db=32, cands=1, kappa=0, k=1, cfg=4)
+    kw.update(args.overrides)
+    w = synth.make_workload(device=dev, name="refine-200k-d128", **kw)
+    n, D = w.X.shape
+    C, d, _ = w.A.shape
+    tags = glv.glv_assign_tags(w.X, w.mu)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    ms_kx, KX = timed(lambda: learn.glv_second_moments(w.X, tags, C))
+    ms_kq, KQ = timed(lambda: learn.glv_second_moments(w.Q))
+    fp64_flops = (n + w.Q.shape[0]) * D * (D + 1)  # multiply-adds of the symmetric halves, x2
+    t0 = time.perf_counter()
+    A0, B0 = learn.sphering_init(w.Q, w.X, tags, C, d)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    P = 4096
+    A = A0.clone().requires_grad_(True)
+    B = B0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([A, B], lr=1e-4)
+
+    def minibatch():
+        qi = torch.randint(0, w.Q.shape[0], (P,), generator=g, device=dev, dtype=torch.int32)
+        xi = torch.randint(0, n, (P,), generator=g, device=dev, dtype=torch.int32)
+        opt.zero_grad(set_to_none=True)
+        loss = learn.pair_loss(A, B, w.Q, w.X, tags, qi, xi)
+        loss.backward()
+        opt.step()
+        return loss
+    for _ in range(args.warmup):
+        minibatch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        minibatch()
+    e1.record()
+    e1.synchronize()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    # one minibatch gradient against the FP64 oracle (relative to the gradient's max entry)
+    import oracle
+    qi = torch.randint(0, w.Q.shape[0], (P,), generator=g, device=dev, dtype=torch.int32)
+    xi = torch.randint(0, n, (P,), generator=g, device=dev, dtype=torch.int32)
+    Ad, Bd = A.detach(), B.detach()
+    s, t, u, v = learn.glv_pair_forward(w.Q, w.X, tags, Ad, Bd, qi, xi)
+    dA, dB = learn.glv_pair_backward(w.Q, w.X, tags, C, qi, xi, u, v, -2.0 * (t - s))
+    qn, xn = qi.cpu().numpy(), xi.cpu().numpy()
+    sub_q, sub_x = np.unique(qn), np.unique(xn)
+    Qs, Xs = w.Q.cpu().numpy()[sub_q], w.X.cpu().numpy()[sub_x]
+    _, gA, gB = oracle.pair_loss_grad(Qs, Xs, tags.cpu().numpy()[sub_x], Ad.cpu().numpy(), Bd.cpu().numpy(),
+                                      np.searchsorted(sub_q, qn), np.searchsorted(sub_x, xn))
+    rel = max(float(np.abs(dA.cpu().numpy() - gA).max() / np.abs(gA).max()),
+              float(np.abs(dB.cpu().numpy() - gB).max() / np.abs(gB).max()))
+    line = {"metric": "refinement minibatches/s (4096 pairs: forward + backward + Adam)",
+            "value": 1e3 / ms_step, "unit": "minibatches/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (moments f64)", "data": "synthetic",
+            "config": {"workload": "refine-200k-d128", "N": n, "nq": int(w.Q.shape[0]), "D": D, "d": d, "C": C,
+                       "pairs_per_minibatch": P},
+            "second_moments": {"ms_database_per_cluster": ms_kx, "ms_queries": ms_kq,
+                               "fp64_tflops": fp64_flops / ((ms_kx + ms_kq) / 1e3) / 1e12},
+            "sphering_init_s": init_s, "pairs_per_s": P * 1e3 / ms_step,
+            "grad_max_rel_err_vs_fp64_oracle": rel}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "refine-200k-d128":
+        return run_learn(args)
     return run_glv(args)
 
 

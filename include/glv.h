@@ -194,16 +194,19 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
 /* ---------------------------------------------------------------------------------------
  * Scoring configuration (the autotuner's hook; no counterpart in the paper).  Per store
  * type: how many lanes of a warp cooperate on one candidate row (1, 2, 4, 8, 16 or 32;
- * 0 = library default) and whether the next candidate's row loads are issued before the
- * current one is computed (pipelined != 0).  The choice changes only speed and the order in
- * which a row's partial dots are summed (FP32 rounding); glv_score_candidates and
- * glv_score_topk always use the same configuration, so their results stay identical.  A
- * choice that cannot serve a row width falls back to the default for that width.
- * glv_get_score_config reports the configuration used for rows of width d.  Process-wide.
+ * 0 = library default) and how rows are gathered (gather_mode): 0 = 16-byte loads into
+ * registers; 1 = the same with the next candidate's loads issued before the current dot;
+ * 2 = one bulk asynchronous copy per row into a per-warp ring of shared-memory slots (used
+ * only where the rings fit in shared memory, else mode 0).  The choice changes only speed
+ * and the order in which a row's partial dots are summed (FP32 rounding); the gather mode
+ * does not change that order, and glv_score_candidates and glv_score_topk always use the
+ * same configuration, so their results stay identical.  A choice that cannot serve a row
+ * width falls back to the default for that width; glv_get_score_config reports the
+ * configuration used for rows of width d.  Process-wide setting.
  * ------------------------------------------------------------------------------------- */
-glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t pipelined);
+glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t gather_mode);
 glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate,
-                                int32_t* pipelined);
+                                int32_t* gather_mode);
 
 /* ---------------------------------------------------------------------------------------
  * Per-query top-kappa of the scores (Algorithm 1: the main step hands kappa candidates to

@@ -1,7 +1,8 @@
 """Autotuner for the gather-score kernels.
 
-The scoring kernels are instantiated for several lanes-per-candidate group sizes, with and
-without software pipelining of the row loads (see csrc/score_launch.cuh).  Which one keeps
+The scoring kernels are instantiated for several lanes-per-candidate group sizes and three
+row-gather modes (register loads, pipelined register loads, bulk copies into shared memory;
+see csrc/score_launch.cuh).  Which one keeps
 HBM busiest depends on the row width, the store type, the candidate-list lengths and the
 GPU, so ``tune_score`` times every offered configuration of the fused score + top-kappa
 call on the caller's own workload (CUDA events on the launching stream, L2 evicted between
@@ -46,28 +47,28 @@ def _save_cache(c: dict) -> None:
 
 def configurations(dt: int):
     for G in glv.SCORE_GROUPS[dt]:
-        for pipe in (False, True):
-            yield G, pipe
+        for mode in glv.GATHER_MODES:
+            yield G, mode
 
 
 def tune_score(index, Q, off, ids, kappa: int, reps: int = 5, use_cache: bool = True, verbose: bool = False):
     """Pick the fastest scoring configuration for ``index``'s store on this workload.
-    Returns (G, pipelined, table) where table maps "G/pipe" to the mean ms per call."""
+    Returns (G, gather_mode, table) where table maps "G/mode" to the mean ms per call."""
     nq = Q.shape[0]
     mean_len = ids.shape[0] / max(nq, 1)
     key = _key(index.dt, index.d, index.C, mean_len)
     cache = _load_cache() if use_cache else {}
     if key in cache:
-        G, pipe = cache[key]["G"], cache[key]["pipe"]
-        glv.glv_set_score_config(index.dt, G, pipe)
-        return G, pipe, cache[key].get("table", {})
+        G, mode = cache[key]["G"], cache[key]["mode"]
+        glv.glv_set_score_config(index.dt, G, mode)
+        return G, mode, cache[key].get("table", {})
     b = index._buffers(nq, ids.shape[0], kappa, kappa)
     glv.glv_project_queries(Q, index.A, index.compute, Qp=b["Qp"], workspace=b["pws"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=Q.device)  # 256 MB > L2
     table = {}
     seen = set()
-    for G, pipe in configurations(index.dt):
-        glv.glv_set_score_config(index.dt, G, pipe)
+    for G, mode in configurations(index.dt):
+        glv.glv_set_score_config(index.dt, G, mode)
         eff = glv.glv_get_score_config(index.dt, index.d)
         if eff in seen:  # this choice cannot serve the row width; it maps onto one already timed
             continue
@@ -89,11 +90,11 @@ def tune_score(index, Q, off, ids, kappa: int, reps: int = 5, use_cache: bool = 
             ms += e0.elapsed_time(e1)
         table[f"{eff[0]}/{int(eff[1])}"] = ms / reps
         if verbose:
-            print(f"  score config G={eff[0]:2d} pipe={int(eff[1])}: {ms / reps:.3f} ms", flush=True)
+            print(f"  score config G={eff[0]:2d} mode={int(eff[1])}: {ms / reps:.3f} ms", flush=True)
     best = min(table, key=table.get)
-    G, pipe = (int(x) for x in best.split("/"))
-    glv.glv_set_score_config(index.dt, G, bool(pipe))
+    G, mode = (int(x) for x in best.split("/"))
+    glv.glv_set_score_config(index.dt, G, mode)
     if use_cache:
-        cache[key] = {"G": G, "pipe": bool(pipe), "table": table}
+        cache[key] = {"G": G, "mode": mode, "table": table}
         _save_cache(cache)
-    return G, bool(pipe), table
+    return G, mode, table

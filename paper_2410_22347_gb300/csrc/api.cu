@@ -186,19 +186,19 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
   return GLV_OK;
 }
 
-glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t pipelined) {
+glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t gather_mode) {
   GLV_CHECK(valid_dt(dt), GLV_ERR_INVALID_ARG);
-  GLV_CHECK(set_score_config(dt, lanes_per_candidate, pipelined != 0), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(set_score_config(dt, lanes_per_candidate, gather_mode), GLV_ERR_INVALID_ARG);
   return GLV_OK;
 }
 
-glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate, int32_t* pipelined) {
-  GLV_CHECK(valid_dt(dt) && d >= 1 && lanes_per_candidate && pipelined, GLV_ERR_INVALID_ARG);
+glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate, int32_t* gather_mode) {
+  GLV_CHECK(valid_dt(dt) && d >= 1 && lanes_per_candidate && gather_mode, GLV_ERR_INVALID_ARG);
   const int nch = (int)(((int64_t)d * elem_bytes(dt) + 15) / 16);
-  int G = 0, pipe = 0;
-  effective_score_config(dt, nch, &G, &pipe);
+  int G = 0, mode = 0;
+  effective_score_config(dt, nch, &G, &mode);
   *lanes_per_candidate = G;
-  *pipelined = pipe;
+  *gather_mode = mode;
   return GLV_OK;
 }
 

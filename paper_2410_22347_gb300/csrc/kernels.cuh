@@ -37,8 +37,8 @@ struct RerankArgs {
 
 cudaError_t launch_score(const ScoreArgs& a, int dt, int64_t nq, int num_sms, cudaStream_t st);
 size_t fused_smem_bytes(int C, int d, int dt);
-bool set_score_config(int dt, int G, bool pipe);
-void effective_score_config(int dt, int nch, int* G, int* pipe);
+bool set_score_config(int dt, int G, int mode);
+void effective_score_config(int dt, int nch, int* G, int* mode);
 cudaError_t launch_score_topk(const ScoreArgs& a, int dt, int64_t nq, int kappa, float* out_s,
                               int32_t* out_id, int num_sms, cudaStream_t st);
 cudaError_t launch_topk(const float* scores, const int64_t* off, const int32_t* ids, int64_t nq,

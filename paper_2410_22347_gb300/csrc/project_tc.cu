@@ -207,7 +207,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int64_t t = blockIdx.x; t < args.num_tiles; t += gridDim.x) {
-      if (!tc::mbar_wait(&tfull[acc], acc_phase, abort_flag)) break;
+      // warp-uniform bounded wait (tcgen05.ld below needs the whole warp)
+      int ok = 0;
+      if (lane == 0) ok = tc::mbar_wait(&tfull[acc], acc_phase, abort_flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      (void)tc::mbar_try_wait(&tfull[acc], acc_phase);
       tc::tc_fence_after();
       const int tm = (int)(t / args.tiles_n), tn = (int)(t % args.tiles_n);
       const int64_t row = (int64_t)tm * kTcBM + q * 32 + lane;

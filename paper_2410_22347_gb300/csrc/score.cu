@@ -9,24 +9,31 @@
 
 #include "kernels.cuh"
 #include "score_launch.cuh"
+#include "score_variants.cuh"
 
 namespace glv {
 
-template <int DT>
-cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, size_t smem, ScoreConfig cfg, cudaStream_t st);
-template <int DT>
-cudaError_t launch_fused_dt(const ScoreArgs& a, int64_t nq, size_t smem, int kappa, float* out_s,
-                            int32_t* out_id, ScoreConfig cfg, cudaStream_t st);
+extern template cudaError_t launch_score_dt<GLV_F32>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
+extern template cudaError_t launch_score_dt<GLV_BF16>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
+extern template cudaError_t launch_score_dt<GLV_FP8_E4M3>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
+extern template cudaError_t launch_fused_dt<GLV_F32>(const ScoreArgs&, int64_t, int, int, float*, int32_t*,
+                                                     ScoreConfig, cudaStream_t);
+extern template cudaError_t launch_fused_dt<GLV_BF16>(const ScoreArgs&, int64_t, int, int, float*, int32_t*,
+                                                      ScoreConfig, cudaStream_t);
+extern template cudaError_t launch_fused_dt<GLV_FP8_E4M3>(const ScoreArgs&, int64_t, int, int, float*, int32_t*,
+                                                          ScoreConfig, cudaStream_t);
+
+constexpr size_t kScoreSmemLimit = 227 * 1024 - 12 * 1024;  // leaves room for static shared memory
 
 static std::mutex g_cfg_mu;
-static ScoreConfig g_cfg[3] = {{0, false}, {0, false}, {0, false}};  // 0 = library default
+static ScoreConfig g_cfg[3] = {{0, 0}, {0, 0}, {0, 0}};  // G = 0: library default
 
-bool set_score_config(int dt, int G, bool pipe) {
-  if (dt < 0 || dt > 2) return false;
+bool set_score_config(int dt, int G, int mode) {
+  if (dt < 0 || dt > 2 || mode < 0 || mode > 2) return false;
   const bool ok = (G == 0) || G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32;
   if (!ok) return false;
   std::lock_guard<std::mutex> lk(g_cfg_mu);
-  g_cfg[dt] = {G, pipe};
+  g_cfg[dt] = {G, mode};
   return true;
 }
 
@@ -47,22 +54,31 @@ static int qstride_of(int d, int dt) {
 ScoreConfig resolve_config(int dt, int nch) {
   const ScoreConfig t = get_score_config(dt);
   switch (dt) {
-    case GLV_F32: return effective_config<GLV_F32>(nch, t.G, t.pipe);
-    case GLV_BF16: return effective_config<GLV_BF16>(nch, t.G, t.pipe);
-    default: return effective_config<GLV_FP8_E4M3>(nch, t.G, t.pipe);
+    case GLV_F32: return effective_config<GLV_F32>(nch, t.G, t.mode);
+    case GLV_BF16: return effective_config<GLV_BF16>(nch, t.G, t.mode);
+    default: return effective_config<GLV_FP8_E4M3>(nch, t.G, t.mode);
   }
 }
 
-void effective_score_config(int dt, int nch, int* G, int* pipe) {
+void effective_score_config(int dt, int nch, int* G, int* mode) {
   const ScoreConfig c = resolve_config(dt, nch);
   *G = c.G;
-  *pipe = c.pipe ? 1 : 0;
+  *mode = c.mode;
+}
+
+// Bulk gather needs its rings in shared memory; if they do not fit, use register loads.
+static ScoreConfig with_rings(ScoreConfig cfg, int C, int qstride, bool fused, int nch, int* RB) {
+  *RB = 0;
+  if (cfg.mode == 2) {
+    *RB = bulk_rows(C, qstride, fused, nch, kScoreSmemLimit);
+    if (*RB == 0) cfg.mode = 0;
+  }
+  return cfg;
 }
 
 cudaError_t launch_score(const ScoreArgs& a0, int dt, int64_t nq, int num_sms, cudaStream_t st) {
   ScoreArgs a = a0;
   a.qstride = qstride_of(a.d, dt);
-  const size_t smem = (size_t)a.C * a.qstride * sizeof(float);
   // enough CTAs to fill the machine a few times over even for few queries
   const int64_t want = (int64_t)num_sms * 8;
   int splits = (int)((want + nq - 1) / nq);
@@ -70,16 +86,18 @@ cudaError_t launch_score(const ScoreArgs& a0, int dt, int64_t nq, int num_sms, c
   if (splits > 64) splits = 64;
   a.splits = splits;
   dim3 grid((unsigned)nq, (unsigned)splits);
-  const ScoreConfig cfg = resolve_config(dt, a.nch);
+  int RB = 0;
+  const ScoreConfig cfg = with_rings(resolve_config(dt, a.nch), a.C, a.qstride, false, a.nch, &RB);
   switch (dt) {
-    case GLV_F32: return launch_score_dt<GLV_F32>(a, grid, smem, cfg, st);
-    case GLV_BF16: return launch_score_dt<GLV_BF16>(a, grid, smem, cfg, st);
-    default: return launch_score_dt<GLV_FP8_E4M3>(a, grid, smem, cfg, st);
+    case GLV_F32: return launch_score_dt<GLV_F32>(a, grid, RB, cfg, st);
+    case GLV_BF16: return launch_score_dt<GLV_BF16>(a, grid, RB, cfg, st);
+    default: return launch_score_dt<GLV_FP8_E4M3>(a, grid, RB, cfg, st);
   }
 }
 
 size_t fused_smem_bytes(int C, int d, int dt) {
-  return (size_t)C * qstride_of(d, dt) * sizeof(float) + (size_t)2048 * sizeof(uint32_t);
+  const int eb = dt == GLV_F32 ? 4 : (dt == GLV_BF16 ? 2 : 1);
+  return score_smem(C, qstride_of(d, dt), true, 0, 0, (d * eb + 15) / 16).total();
 }
 
 cudaError_t launch_score_topk(const ScoreArgs& a0, int dt, int64_t nq, int kappa, float* out_s,
@@ -94,12 +112,12 @@ cudaError_t launch_score_topk(const ScoreArgs& a0, int dt, int64_t nq, int kappa
   ScoreArgs a = a0;
   a.qstride = qstride_of(a.d, dt);
   a.splits = 1;
-  const size_t smem = fused_smem_bytes(a.C, a.d, dt);
-  const ScoreConfig cfg = resolve_config(dt, a.nch);
+  int RB = 0;
+  const ScoreConfig cfg = with_rings(resolve_config(dt, a.nch), a.C, a.qstride, true, a.nch, &RB);
   switch (dt) {
-    case GLV_F32: return launch_fused_dt<GLV_F32>(a, nq, smem, kappa, out_s, out_id, cfg, st);
-    case GLV_BF16: return launch_fused_dt<GLV_BF16>(a, nq, smem, kappa, out_s, out_id, cfg, st);
-    default: return launch_fused_dt<GLV_FP8_E4M3>(a, nq, smem, kappa, out_s, out_id, cfg, st);
+    case GLV_F32: return launch_fused_dt<GLV_F32>(a, nq, RB, kappa, out_s, out_id, cfg, st);
+    case GLV_BF16: return launch_fused_dt<GLV_BF16>(a, nq, RB, kappa, out_s, out_id, cfg, st);
+    default: return launch_fused_dt<GLV_FP8_E4M3>(a, nq, RB, kappa, out_s, out_id, cfg, st);
   }
 }
 

@@ -1,10 +1,11 @@
 // score_variants.cuh -- the stand-alone scoring kernel and the fused scoring + top-kappa
-// kernel as templates over (store type, lanes per candidate, loads per lane, pipelining),
-// with the launchers that instantiate them for one store type (one translation unit per
-// store type: score_f32.cu, score_bf16.cu, score_fp8.cu).
+// kernel as templates over (store type, lanes per candidate G, loads per lane NCH, gather
+// mode), with the launchers that instantiate them for one store type (one translation unit
+// per store type: score_f32.cu, score_bf16.cu, score_fp8.cu).
 #pragma once
 
 #include "kernels.cuh"
+#include "score_bulk.cuh"
 #include "score_dev.cuh"
 #include "score_launch.cuh"
 #include "topk_dev.cuh"
@@ -12,64 +13,133 @@
 namespace glv {
 
 constexpr int kFusedCache = 2048;  // list entries kept as keys in shared memory
+constexpr int kBulkSlots = 2;      // ring slots per warp (bulk gather)
+constexpr int kScoreThreads = 256;
+
+// Shared-memory carve-up shared by host and device: [projected query | keys | rings | bars].
+struct ScoreSmem {
+  size_t qs_bytes, keys_bytes, ring_bytes, bar_bytes;
+  __host__ __device__ size_t total() const { return qs_bytes + keys_bytes + ring_bytes + bar_bytes; }
+};
+
+__host__ __device__ inline ScoreSmem score_smem(int C, int qstride, bool fused, int mode, int RB, int nch) {
+  ScoreSmem m;
+  m.qs_bytes = (((size_t)C * qstride * sizeof(float)) + 127) & ~size_t(127);
+  m.keys_bytes = fused ? (size_t)kFusedCache * sizeof(uint32_t) : 0;
+  const int warps = kScoreThreads / 32;
+  m.ring_bytes = mode == 2 ? (size_t)warps * kBulkSlots * RB * nch * 16 : 0;
+  m.bar_bytes = mode == 2 ? (size_t)warps * kBulkSlots * sizeof(uint64_t) : 0;
+  return m;
+}
+
+// Rows per bulk batch: the largest of 32, 16, 8 whose rings fit next to the rest.
+inline int bulk_rows(int C, int qstride, bool fused, int nch, size_t limit) {
+  for (int RB = 32; RB >= 8; RB /= 2)
+    if (score_smem(C, qstride, fused, 2, RB, nch).total() <= limit) return RB;
+  return 0;
+}
+
+template <int DT, int G, int NCH, int MODE, class Sink>
+GLV_DEV void score_span(const ScoreArgs& a, uint8_t* smem, const ScoreSmem& L, int RB, int64_t b0, int64_t b1,
+                        Sink& sink, volatile int* abort) {
+  const float* qs = reinterpret_cast<const float*>(smem);
+  if constexpr (MODE == 2) {
+    uint8_t* ring = smem + L.qs_bytes + L.keys_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + L.ring_bytes);
+    const int warp = threadIdx.x >> 5;
+    const size_t per_warp = (size_t)kBulkSlots * RB * a.nch * 16;
+    score_range_bulk<DT, G, NCH, kBulkSlots>(a, qs, ring + warp * per_warp, bars + warp * kBulkSlots, RB, b0, b1,
+                                             sink, abort);
+  } else {
+    score_range<DT, G, NCH, MODE == 1>(a, qs, b0, b1, sink);
+  }
+}
+
+template <int MODE>
+GLV_DEV void init_bulk_bars(uint8_t* smem, const ScoreSmem& L) {
+  if constexpr (MODE == 2) {
+    if (threadIdx.x == 0) {
+      uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.qs_bytes + L.keys_bytes + L.ring_bytes);
+      for (int t = 0; t < (kScoreThreads / 32) * kBulkSlots; ++t) tc::mbar_init(&bars[t], 1);
+      tc::fence_mbar_init();
+    }
+  }
+}
 
 // One CTA per (query, split of its candidate list): the query's C projected views are staged
 // once in shared memory, so every candidate, whatever its cluster, finds its q_c on chip (the
 // "eager" inner product of the paper).
-template <int DT, int G, int NCH, bool PIPE>
-__global__ void __launch_bounds__(256) score_kernel(const ScoreArgs a) {
-  extern __shared__ __align__(16) float qs[];
+template <int DT, int G, int NCH, int MODE>
+__global__ void __launch_bounds__(kScoreThreads) score_kernel(const ScoreArgs a, int RB) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ int abort_flag;
+  const ScoreSmem L = score_smem(a.C, a.qstride, false, MODE, RB, a.nch);
+  if (threadIdx.x == 0) abort_flag = 0;
+  init_bulk_bars<MODE>(smem, L);
   const int64_t j = blockIdx.x;
-  stage_qp<DT>(a, j, qs);
+  stage_qp<DT>(a, j, reinterpret_cast<float*>(smem));
   __syncthreads();
   const int64_t p0 = a.off[j], p1 = a.off[j + 1];
   const int64_t per = (p1 - p0 + a.splits - 1) / a.splits;
   const int64_t b0 = p0 + (int64_t)blockIdx.y * per;
   const int64_t b1 = min(p1, b0 + per);
   float* scores = a.scores;
-  score_range<DT, G, NCH, PIPE>(a, qs, b0, b1, [scores](int64_t p, float s) { scores[p] = s; });
+  auto sink = [scores](int64_t p, float s) { scores[p] = s; };
+  score_span<DT, G, NCH, MODE>(a, smem, L, RB, b0, b1, sink, &abort_flag);
+  if (MODE == 2) {
+    __syncthreads();
+    if (threadIdx.x == 0 && abort_flag) report(a.d_status, GLV_ERR_TIMEOUT);
+  }
 }
 
 // Gather-score and top-kappa of one query in one CTA: scores stay on chip as order-preserving
 // keys in shared memory and the radix selection runs there; a list longer than kFusedCache
 // spills its scores to the caller's scratch (L2-resident during the selection passes).
-template <int DT, int G, int NCH, bool PIPE>
-__global__ void __launch_bounds__(256, PIPE ? 3 : 5) score_topk_kernel(const ScoreArgs a, int kappa, float* out_s,
-                                                            int32_t* out_id) {
-  extern __shared__ __align__(16) float smem[];
+template <int DT, int G, int NCH, int MODE>
+__global__ void __launch_bounds__(kScoreThreads, MODE == 1 ? 3 : (MODE == 2 ? 1 : 5))
+    score_topk_kernel(const ScoreArgs a, int RB, int kappa, float* out_s, int32_t* out_id) {
+  extern __shared__ __align__(128) uint8_t smem[];
   __shared__ TopkSmem S;
-  float* qs = smem;
-  uint32_t* kc = reinterpret_cast<uint32_t*>(smem + (size_t)a.C * a.qstride);
+  __shared__ int abort_flag;
+  const ScoreSmem L = score_smem(a.C, a.qstride, true, MODE, RB, a.nch);
+  uint32_t* kc = reinterpret_cast<uint32_t*>(smem + L.qs_bytes);
+  if (threadIdx.x == 0) abort_flag = 0;
+  init_bulk_bars<MODE>(smem, L);
   const int64_t j = blockIdx.x;
-  stage_qp<DT>(a, j, qs);
+  stage_qp<DT>(a, j, reinterpret_cast<float*>(smem));
   __syncthreads();
   const int64_t p0 = a.off[j], p1 = a.off[j + 1];
-  const int64_t L = p1 - p0;
-  const bool cached = L <= kFusedCache;
+  const int64_t L_ = p1 - p0;
+  const bool cached = L_ <= kFusedCache;
   float* scores = a.scores;
-  if (cached)
-    score_range<DT, G, NCH, PIPE>(a, qs, p0, p1, [kc, p0](int64_t p, float s) { kc[p - p0] = score_key(s); });
-  else
-    score_range<DT, G, NCH, PIPE>(a, qs, p0, p1, [scores](int64_t p, float s) { scores[p] = s; });
+  if (cached) {
+    auto sink = [kc, p0](int64_t p, float s) { kc[p - p0] = score_key(s); };
+    score_span<DT, G, NCH, MODE>(a, smem, L, RB, p0, p1, sink, &abort_flag);
+  } else {
+    auto sink = [scores](int64_t p, float s) { scores[p] = s; };
+    score_span<DT, G, NCH, MODE>(a, smem, L, RB, p0, p1, sink, &abort_flag);
+  }
   __syncthreads();
+  if (MODE == 2 && threadIdx.x == 0 && abort_flag) report(a.d_status, GLV_ERR_TIMEOUT);
   const float* sj = scores + p0;
   const int32_t* ij = a.ids + p0;
   select_topk(
-      S, L, kappa, [&](int64_t p) -> uint32_t { return cached ? kc[p] : score_key(sj[p]); },
+      S, L_, kappa, [&](int64_t p) -> uint32_t { return cached ? kc[p] : score_key(sj[p]); },
       [&](int64_t p) -> int32_t { return ij[p]; }, out_s + j * kappa, out_id + j * kappa);
 }
 
 struct ScoreLaunch {
   const ScoreArgs& a;
   dim3 grid;
-  size_t smem;
+  int RB;
   cudaStream_t st;
-  template <int DT, int G, int NCH, bool PIPE>
+  template <int DT, int G, int NCH, int MODE>
   cudaError_t go() {
-    auto k = score_kernel<DT, G, NCH, PIPE>;
+    auto k = score_kernel<DT, G, NCH, MODE>;
+    const size_t smem = score_smem(a.C, a.qstride, false, MODE, RB, a.nch).total();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 256, smem, st>>>(a);
+    k<<<grid, kScoreThreads, smem, st>>>(a, RB);
     return cudaGetLastError();
   }
 };
@@ -77,37 +147,39 @@ struct ScoreLaunch {
 struct FusedLaunch {
   const ScoreArgs& a;
   int64_t nq;
-  size_t smem;
+  int RB;
   int kappa;
   float* out_s;
   int32_t* out_id;
   cudaStream_t st;
-  template <int DT, int G, int NCH, bool PIPE>
+  template <int DT, int G, int NCH, int MODE>
   cudaError_t go() {
-    auto k = score_topk_kernel<DT, G, NCH, PIPE>;
+    auto k = score_topk_kernel<DT, G, NCH, MODE>;
+    const size_t smem = score_smem(a.C, a.qstride, true, MODE, RB, a.nch).total();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)nq, 256, smem, st>>>(a, kappa, out_s, out_id);
+    k<<<(unsigned)nq, kScoreThreads, smem, st>>>(a, RB, kappa, out_s, out_id);
     return cudaGetLastError();
   }
 };
 
 template <int DT>
-cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, size_t smem, ScoreConfig cfg, cudaStream_t st) {
-  ScoreLaunch f{a, grid, smem, st};
-  return dispatch_score<DT>(cfg.G, a.nch, cfg.pipe, f);
+cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, int RB, ScoreConfig cfg, cudaStream_t st) {
+  ScoreLaunch f{a, grid, RB, st};
+  return dispatch_score<DT>(cfg.G, a.nch, cfg.mode, f);
 }
 
 template <int DT>
-cudaError_t launch_fused_dt(const ScoreArgs& a, int64_t nq, size_t smem, int kappa, float* out_s,
-                            int32_t* out_id, ScoreConfig cfg, cudaStream_t st) {
-  FusedLaunch f{a, nq, smem, kappa, out_s, out_id, st};
-  return dispatch_score<DT>(cfg.G, a.nch, cfg.pipe, f);
+cudaError_t launch_fused_dt(const ScoreArgs& a, int64_t nq, int RB, int kappa, float* out_s, int32_t* out_id,
+                            ScoreConfig cfg, cudaStream_t st) {
+  FusedLaunch f{a, nq, RB, kappa, out_s, out_id, st};
+  return dispatch_score<DT>(cfg.G, a.nch, cfg.mode, f);
 }
 
-#define GLV_INSTANTIATE_SCORE(DT)                                                                       \
-  template cudaError_t launch_score_dt<DT>(const ScoreArgs&, dim3, size_t, ScoreConfig, cudaStream_t); \
-  template cudaError_t launch_fused_dt<DT>(const ScoreArgs&, int64_t, size_t, int, float*, int32_t*,    \
+#define GLV_INSTANTIATE_SCORE_PLAIN(DT) \
+  template cudaError_t launch_score_dt<DT>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
+#define GLV_INSTANTIATE_SCORE_FUSED(DT)                                                            \
+  template cudaError_t launch_fused_dt<DT>(const ScoreArgs&, int64_t, int, int, float*, int32_t*, \
                                            ScoreConfig, cudaStream_t);
 
 }  // namespace glv

@@ -230,15 +230,18 @@ def glv_score_topk(Qp, Xred, row_stride: int, scales, dt: int, tags, off, ids, k
 SCORE_GROUPS = {GLV_F32: (4, 8, 16, 32), GLV_BF16: (2, 4, 8, 32), GLV_FP8_E4M3: (1, 2, 4, 32)}
 
 
-def glv_set_score_config(dt: int, lanes_per_candidate: int, pipelined: bool) -> None:
-    _check("glv_set_score_config", _lib.glv_set_score_config(dt, int(lanes_per_candidate), int(bool(pipelined))))
+GATHER_MODES = (0, 1, 2)  # registers, registers pipelined, bulk copies into shared memory
 
 
-def glv_get_score_config(dt: int, d: int) -> tuple[int, bool]:
+def glv_set_score_config(dt: int, lanes_per_candidate: int, gather_mode: int) -> None:
+    _check("glv_set_score_config", _lib.glv_set_score_config(dt, int(lanes_per_candidate), int(gather_mode)))
+
+
+def glv_get_score_config(dt: int, d: int) -> tuple[int, int]:
     g = ctypes.c_int32(0)
     p = ctypes.c_int32(0)
     _check("glv_get_score_config", _lib.glv_get_score_config(dt, int(d), ctypes.byref(g), ctypes.byref(p)))
-    return int(g.value), bool(p.value)
+    return int(g.value), int(p.value)
 
 
 def glv_topk(scores, off, ids, kappa: int, out_s=None, out_id=None, stream=None):

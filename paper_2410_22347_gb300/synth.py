@@ -198,6 +198,7 @@ WORKLOADS = {
 
 
 def workload(name: str, device="cpu", **override) -> Workload:
+    """One of the named workloads, drawn on ``device``; keyword overrides change its fields."""
     kw = dict(WORKLOADS[name])
     kw.update(override)
     return make_workload(device=device, name=name, **kw)

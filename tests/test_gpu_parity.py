@@ -490,22 +490,41 @@ def test_every_score_configuration_matches_oracle(glv, dt_name):
     dt = glv.DTYPES[dt_name]
     try:
         for G in glv.SCORE_GROUPS[dt]:
-            for pipe in (False, True):
-                glv.glv_set_score_config(dt, G, pipe)
+            for mode in glv.GATHER_MODES:
+                glv.glv_set_score_config(dt, G, mode)
                 for d in (27, 160):
                     _score_case(glv, dt, 300 + G + d, d, 5, [0, 1, 700, 33, 2100, 1500], N=2500, D=max(d, 64))
+                    _score_case(glv, dt, 301 + G + d, d, 5, [0, 1, 700, 33, 2100, 1500], N=2500, D=max(d, 64),
+                                bad_ids=True)
     finally:
-        glv.glv_set_score_config(dt, 0, False)
+        glv.glv_set_score_config(dt, 0, 0)
+
+
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_fused_matches_separate_in_every_gather_mode(glv, dt_name, mode):
+    """Gather modes change only how rows travel; the scores (and so the selections) of the
+    fused and the stand-alone paths stay bit-identical."""
+    dt = glv.DTYPES[dt_name]
+    try:
+        glv.glv_set_score_config(dt, glv.SCORE_GROUPS[dt][1], mode)
+        test_score_topk_fused_matches_separate(glv, dt_name, 700, 100)
+    finally:
+        glv.glv_set_score_config(dt, 0, 0)
 
 
 def test_score_config_roundtrip(glv):
     try:
-        glv.glv_set_score_config(glv.GLV_BF16, 8, True)
-        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, True)
+        glv.glv_set_score_config(glv.GLV_BF16, 8, 1)
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, 1)
         # 8 lanes x 5 pipelined loads cannot cover a 160-chunk row: falls back to a default
-        g, p = glv.glv_get_score_config(glv.GLV_BF16, 1280)
-        assert not p
+        g, m = glv.glv_get_score_config(glv.GLV_BF16, 1280)
+        assert m == 0
+        glv.glv_set_score_config(glv.GLV_BF16, 4, 2)
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (4, 2)
         with pytest.raises(glv.GlvError):
-            glv.glv_set_score_config(glv.GLV_BF16, 3, False)
+            glv.glv_set_score_config(glv.GLV_BF16, 3, 0)
+        with pytest.raises(glv.GlvError):
+            glv.glv_set_score_config(glv.GLV_BF16, 4, 3)
     finally:
-        glv.glv_set_score_config(glv.GLV_BF16, 0, False)
+        glv.glv_set_score_config(glv.GLV_BF16, 0, 0)
