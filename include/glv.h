@@ -70,13 +70,28 @@ int64_t glv_min_row_stride(int32_t d, glv_dtype dt);
 
 /* ---------------------------------------------------------------------------------------
  * Cluster tags, Eq. (cluster_tag), Section 4:  c_i = argmax_c <x_i, mu_c>.
- *   X    : N x D float32, rows contiguous.
- *   mu   : C x D float32 landmarks.
- *   tags : N uint16 output.  Ties go to the lowest c.  FP32 accumulation.
- * Limits: C * D * 4 bytes must fit in shared memory (C * D <= 49152).
+ *   X       : N x D float32, rows contiguous.
+ *   mu      : C x D float32 landmarks.
+ *   tags    : N uint16 output.  Ties go to the lowest c.  FP32 accumulation.
+ *   best_ip : N float32 output <x_i, mu_{c_i}> (may be NULL) -- the spherical k-means
+ *             objective terms (Appendix A) and the k-means++ seeding weights.
+ * Limits: D <= 1024 and C * D * 4 bytes must fit in shared memory (C * D <= 58112).
  * ------------------------------------------------------------------------------------- */
 glv_status glv_assign_tags(const float* X, int64_t N, int32_t D, const float* mu, int32_t C,
-                           uint16_t* tags, void* stream);
+                           uint16_t* tags, float* best_ip, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Spherical k-means M-step, Appendix A:  mu_c = sum_{i: tags_i = c} x_i / || . ||_2
+ * (FP64 sums; a cluster with no member keeps its landmark).  With glv_assign_tags as the
+ * E-step this is the landmark learning of Algorithm 5 (rows are expected L2-normalised).
+ *   X : N x D float32;  tags : N uint16;  mu : C x D float32, updated in place.
+ *   counts : C int32 output cluster sizes (may be NULL).
+ *   workspace : glv_kmeans_workspace_size(N, D, C) bytes, 256-aligned.
+ * ------------------------------------------------------------------------------------- */
+size_t glv_kmeans_workspace_size(int64_t N, int32_t D, int32_t C);
+glv_status glv_kmeans_update(const float* X, int64_t N, int32_t D, const uint16_t* tags,
+                             int32_t C, float* mu, int32_t* counts, void* workspace,
+                             int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Reduced database, Eq. (X_low), Section 4, read as x_i^low = g_{c_i}(x_i) = B_{c_i} x_i

@@ -70,6 +70,8 @@ def _load():
         "glvo_quantize_fp8_rows": (None, [P, i64, i32, P, P]),
         "glvo_pair_loss_grad": (f64, [P, P, i32, P, P, P, i32, i32, P, P, i64, P, P]),
         "glvo_second_moment": (None, [P, i64, i32, P, i32, P]),
+        "glvo_kmeans_update": (None, [P, i64, i32, P, i32, P, P, P]),
+        "glvo_spherical_objective": (f64, [P, i64, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -334,3 +336,30 @@ def gleanvec_sphering(Q_learn, X_learn, tags, C: int, d: int):
         KX = second_moment(X_learn, tags, c)
         A[c], B[c], _, _ = sphering_from_moments(KQ, KX, d)
     return A, B
+
+
+# ------------------------------------------------------------------------------------
+# spherical k-means (Appendix A)
+# ------------------------------------------------------------------------------------
+
+def kmeans_update(X, tags, mu_in):
+    """M-step of spherical k-means: mu_c = normalised sum of the rows tagged c (FP64); a
+    cluster without members keeps its landmark.  Returns (mu FP64 C x D, counts)."""
+    X = _c(X, np.float32)
+    tags = _c(tags, np.uint16)
+    mu_in = _c(mu_in, np.float32)
+    N, D = X.shape
+    C = mu_in.shape[0]
+    mu = np.empty((C, D), np.float64)
+    counts = np.empty(C, np.int64)
+    _load().glvo_kmeans_update(_p(X), N, D, _p(tags), C, _p(mu_in), _p(mu), _p(counts))
+    return mu, counts
+
+
+def spherical_objective(X, mu, tags):
+    """Appendix A objective sum_i <x_i, mu_{c_i}>."""
+    X = _c(X, np.float32)
+    mu = _c(mu, np.float32)
+    tags = _c(tags, np.uint16)
+    N, D = X.shape
+    return float(_load().glvo_spherical_objective(_p(X), N, D, _p(mu), _p(tags)))

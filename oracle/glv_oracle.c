@@ -466,3 +466,41 @@ void glvo_second_moment(const float* V, int64_t n, int32_t D, const uint16_t* ta
       K[(int64_t)a * D + b] = v;
     }
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Spherical k-means, Appendix A: the M-step mu_c = sum_{i: c_i = c} x_i / ||...||_2      */
+/* (rows of X are taken as given; the caller normalises them).  A cluster with no member  */
+/* (or a zero sum) keeps its previous landmark.  counts (may be NULL) receives |X_c|.     */
+/* ------------------------------------------------------------------------------------ */
+void glvo_kmeans_update(const float* X, int64_t N, int32_t D, const uint16_t* tags, int32_t C,
+                        const float* mu_in, double* mu_out, int64_t* counts) {
+  double* sum = (double*)calloc((size_t)C * (size_t)D, sizeof(double));
+  int64_t* cnt = (int64_t*)calloc((size_t)C, sizeof(int64_t));
+  for (int64_t i = 0; i < N; ++i) {
+    const int64_t c = tags[i];
+    if (c >= C) continue;
+    cnt[c] += 1;
+    for (int32_t k = 0; k < D; ++k) sum[c * D + k] += (double)X[i * D + k];
+  }
+  for (int64_t c = 0; c < C; ++c) {
+    double nrm = 0.0;
+    for (int32_t k = 0; k < D; ++k) nrm += sum[c * D + k] * sum[c * D + k];
+    nrm = sqrt(nrm);
+    for (int32_t k = 0; k < D; ++k)
+      mu_out[c * D + k] = (cnt[c] > 0 && nrm > 0.0) ? sum[c * D + k] / nrm : (double)mu_in[c * D + k];
+    if (counts) counts[c] = cnt[c];
+  }
+  free(sum);
+  free(cnt);
+}
+
+/* Spherical k-means objective of Appendix A: sum_i <x_i, mu_{c_i}>. */
+double glvo_spherical_objective(const float* X, int64_t N, int32_t D, const float* mu, const uint16_t* tags) {
+  double obj = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    double v = 0.0;
+    for (int32_t k = 0; k < D; ++k) v += (double)X[i * D + k] * (double)mu[(int64_t)tags[i] * D + k];
+    obj += v;
+  }
+  return obj;
+}

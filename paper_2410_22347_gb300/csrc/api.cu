@@ -97,12 +97,12 @@ int64_t glv_min_row_stride(int32_t d, glv_dtype dt) {
 }
 
 glv_status glv_assign_tags(const float* X, int64_t N, int32_t D, const float* mu, int32_t C,
-                           uint16_t* tags, void* stream) {
+                           uint16_t* tags, float* best_ip, void* stream) {
   GLV_CHECK(N >= 0 && D >= 1 && C >= 1 && C <= 65536, GLV_ERR_INVALID_ARG);
   if (N == 0) return GLV_OK;
   GLV_CHECK(X && mu && tags, GLV_ERR_INVALID_ARG);
   GLV_CHECK(D <= 1024 && (size_t)C * D * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
-  GLV_LAUNCH(launch_tags(X, N, D, mu, C, tags, num_sms(), (cudaStream_t)stream));
+  GLV_LAUNCH(launch_tags(X, N, D, mu, C, tags, best_ip, num_sms(), (cudaStream_t)stream));
   return GLV_OK;
 }
 
@@ -293,6 +293,19 @@ glv_status glv_pair_backward(const float* Q, int64_t nQ, const float* X, int64_t
   }
   GLV_LAUNCH(launch_pair_backward(Q, nQ, X, nX, D, tags, C, d, qi, xi, P, u, v, g, dA, dB, workspace, d_status,
                                   (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+size_t glv_kmeans_workspace_size(int64_t N, int32_t D, int32_t C) {
+  if (N < 0 || D < 1 || C < 1) return 0;
+  return kmeans_ws_bytes(N, C, D);
+}
+
+glv_status glv_kmeans_update(const float* X, int64_t N, int32_t D, const uint16_t* tags, int32_t C, float* mu,
+                             int32_t* counts, void* workspace, int32_t* d_status, void* stream) {
+  GLV_CHECK(N >= 0 && N <= 2147483647LL && D >= 1 && C >= 1 && C <= 65535, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(mu && (N == 0 || (X && tags)) && workspace && aligned(workspace, 256), GLV_ERR_INVALID_ARG);
+  GLV_LAUNCH(launch_kmeans_update(X, N, D, tags, C, mu, counts, workspace, d_status, (cudaStream_t)stream));
   return GLV_OK;
 }
 

@@ -63,6 +63,9 @@ BuildWs build_ws_carve(void* ws, int64_t N, int C);
 cudaError_t launch_grouping(const uint16_t* tags, int64_t N, int C, const BuildWs& ws, int32_t* d_status,
                             cudaStream_t st);
 size_t build_ws_bytes(int64_t N, int C);
+size_t kmeans_ws_bytes(int64_t N, int C, int D);
+cudaError_t launch_kmeans_update(const float* X, int64_t N, int D, const uint16_t* tags, int C, float* mu,
+                                 int32_t* counts_out, void* ws, int32_t* d_status, cudaStream_t st);
 size_t moments_ws_bytes(int64_t n, int C);
 cudaError_t launch_moments(const float* V, int64_t n, int D, const uint16_t* tags, int C, double* K, void* ws,
                            int32_t* d_status, cudaStream_t st);
@@ -79,6 +82,6 @@ cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags,
                          int C, int d, int dt, void* Xred, int64_t row_stride, float* scales,
                          void* workspace, int32_t* d_status, cudaStream_t st);
 cudaError_t launch_tags(const float* X, int64_t N, int D, const float* mu, int C, uint16_t* tags,
-                        int num_sms, cudaStream_t st);
+                        float* best_ip, int num_sms, cudaStream_t st);
 
 }  // namespace glv

@@ -12,7 +12,7 @@ namespace glv {
 template <int NPL>  // row elements per lane (D <= 32 * NPL)
 __global__ void __launch_bounds__(256) tags_kernel(const float* __restrict__ X, int64_t N, int D,
                                                    const float* __restrict__ mu, int C,
-                                                   uint16_t* __restrict__ tags) {
+                                                   uint16_t* __restrict__ tags, float* __restrict__ best_ip) {
   extern __shared__ float ms[];  // C x D
   for (int t = threadIdx.x; t < C * D; t += blockDim.x) ms[t] = mu[t];
   __syncthreads();
@@ -42,12 +42,15 @@ __global__ void __launch_bounds__(256) tags_kernel(const float* __restrict__ X, 
         bc = c;
       }
     }
-    if (lane == 0) tags[i] = (uint16_t)bc;
+    if (lane == 0) {
+      tags[i] = (uint16_t)bc;
+      if (best_ip) best_ip[i] = best;
+    }
   }
 }
 
 cudaError_t launch_tags(const float* X, int64_t N, int D, const float* mu, int C, uint16_t* tags,
-                        int num_sms, cudaStream_t st) {
+                        float* best_ip, int num_sms, cudaStream_t st) {
   const size_t smem = (size_t)C * D * sizeof(float);
   int64_t blocks = (N + 7) / 8;
   const int64_t cap = (int64_t)num_sms * 8;
@@ -58,7 +61,7 @@ cudaError_t launch_tags(const float* X, int64_t N, int D, const float* mu, int C
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                          (int)smem);                                     \
     if (e != cudaSuccess) return e;                                                      \
-    k<<<(unsigned)blocks, 256, smem, st>>>(X, N, D, mu, C, tags);                        \
+    k<<<(unsigned)blocks, 256, smem, st>>>(X, N, D, mu, C, tags, best_ip);               \
     return cudaGetLastError();                                                           \
   }
   const int npl = (D + 31) / 32;
@@ -68,6 +71,71 @@ cudaError_t launch_tags(const float* X, int64_t N, int D, const float* mu, int C
   if (npl <= 32) GLV_TAGS(32)
 #undef GLV_TAGS
   return cudaErrorInvalidValue;
+}
+
+}  // namespace glv
+
+// ---- spherical k-means M-step (Appendix A) -------------------------------------------------
+//   mu_c = sum_{i: c_i = c} x_i / || . ||_2, rows grouped by cluster (launch_grouping); FP64
+//   sums, one CTA per (cluster, 128-column block); a cluster without members (or with a zero
+//   sum) keeps its landmark.
+
+namespace glv {
+
+__global__ void __launch_bounds__(128) kmeans_sum_kernel(const float* __restrict__ X, int D, BuildWs g,
+                                                         double* __restrict__ sums) {
+  const int c = blockIdx.x;
+  const int k = blockIdx.y * 128 + threadIdx.x;
+  if (k >= D) return;
+  const int64_t start = g.seg_start[c], cnt = g.counts[c];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t r = 0;
+  for (; r + 4 <= cnt; r += 4) {
+    s0 += (double)X[(int64_t)g.perm[start + r] * D + k];
+    s1 += (double)X[(int64_t)g.perm[start + r + 1] * D + k];
+    s2 += (double)X[(int64_t)g.perm[start + r + 2] * D + k];
+    s3 += (double)X[(int64_t)g.perm[start + r + 3] * D + k];
+  }
+  for (; r < cnt; ++r) s0 += (double)X[(int64_t)g.perm[start + r] * D + k];
+  sums[(int64_t)c * D + k] = (s0 + s1) + (s2 + s3);
+}
+
+__global__ void __launch_bounds__(256) kmeans_normalize_kernel(const double* __restrict__ sums, int D,
+                                                               const int32_t* __restrict__ counts,
+                                                               float* __restrict__ mu) {
+  __shared__ double part[256];
+  const int c = blockIdx.x;
+  double q = 0.0;
+  for (int k = threadIdx.x; k < D; k += blockDim.x) {
+    const double v = sums[(int64_t)c * D + k];
+    q += v * v;
+  }
+  part[threadIdx.x] = q;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double nrm = sqrt(part[0]);
+  if (counts[c] == 0 || !(nrm > 0.0)) return;  // keep the previous landmark
+  for (int k = threadIdx.x; k < D; k += blockDim.x) mu[(int64_t)c * D + k] = (float)(sums[(int64_t)c * D + k] / nrm);
+}
+
+size_t kmeans_ws_bytes(int64_t N, int C, int D) {
+  return ((size_t)C * D * sizeof(double) + 255) / 256 * 256 + build_ws_bytes(N, C);
+}
+
+cudaError_t launch_kmeans_update(const float* X, int64_t N, int D, const uint16_t* tags, int C, float* mu,
+                                 int32_t* counts_out, void* ws, int32_t* d_status, cudaStream_t st) {
+  double* sums = static_cast<double*>(ws);
+  BuildWs g = build_ws_carve(static_cast<char*>(ws) + ((size_t)C * D * sizeof(double) + 255) / 256 * 256, N, C);
+  cudaError_t e = launch_grouping(tags, N, C, g, d_status, st);
+  if (e != cudaSuccess) return e;
+  kmeans_sum_kernel<<<dim3(C, (D + 127) / 128), 128, 0, st>>>(X, D, g, sums);
+  kmeans_normalize_kernel<<<C, 256, 0, st>>>(sums, D, g.counts, mu);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (counts_out) e = cudaMemcpyAsync(counts_out, g.counts, sizeof(int32_t) * C, cudaMemcpyDeviceToDevice, st);
+  return e;
 }
 
 }  // namespace glv

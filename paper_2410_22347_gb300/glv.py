@@ -39,7 +39,9 @@ def _load() -> ctypes.CDLL:
         "glv_abi_version": (i32, []),
         "glv_status_string": (ctypes.c_char_p, [i32]),
         "glv_min_row_stride": (i64, [i32, i32]),
-        "glv_assign_tags": (i32, [P, i64, i32, P, i32, P, P]),
+        "glv_assign_tags": (i32, [P, i64, i32, P, i32, P, P, P]),
+        "glv_kmeans_workspace_size": (sz, [i64, i32, i32]),
+        "glv_kmeans_update": (i32, [P, i64, i32, P, i32, P, P, P, P, P]),
         "glv_build_reduced_workspace_size": (sz, [i64, i32]),
         "glv_build_reduced": (i32, [P, i64, i32, P, P, i32, i32, i32, P, i64, P, P, P, P]),
         "glv_build_reduced_noalloc": (i32, [P, i64, i32, P, P, i32, i32, i32, P, i64, P, P, P]),
@@ -112,16 +114,33 @@ def elem_bytes(dt: int) -> int:
 # ---------------------------------------------------------------------------------------
 
 def glv_assign_tags(X: torch.Tensor, mu: torch.Tensor, tags: torch.Tensor | None = None,
-                    stream=None) -> torch.Tensor:
+                    best_ip: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     _need(X, torch.float32, "X", 2)
     _need(mu, torch.float32, "mu", 2)
     N, D = X.shape
     if tags is None:
         tags = torch.empty(N, dtype=torch.uint16, device=X.device)
     _need(tags, torch.uint16, "tags", 1)
+    if best_ip is not None:
+        _need(best_ip, torch.float32, "best_ip", 1)
     _check("glv_assign_tags", _lib.glv_assign_tags(_ptr(X), N, D, _ptr(mu), mu.shape[0], _ptr(tags),
-                                                   _stream(stream)))
+                                                   _ptr(best_ip), _stream(stream)))
     return tags
+
+
+def glv_kmeans_update(X, tags, mu, counts=None, d_status=None, stream=None):
+    """Spherical k-means M-step in place on mu (C x D); returns (mu, counts)."""
+    _need(X, torch.float32, "X", 2)
+    _need(tags, torch.uint16, "tags", 1)
+    _need(mu, torch.float32, "mu", 2)
+    N, D = X.shape
+    C = mu.shape[0]
+    if counts is None:
+        counts = torch.empty(C, dtype=torch.int32, device=X.device)
+    ws = torch.empty(max(int(_lib.glv_kmeans_workspace_size(N, D, C)), 1), dtype=torch.uint8, device=X.device)
+    _check("glv_kmeans_update", _lib.glv_kmeans_update(_ptr(X), N, D, _ptr(tags), C, _ptr(mu), _ptr(counts),
+                                                       _ptr(ws), _ptr(d_status), _stream(stream)))
+    return mu, counts
 
 
 def glv_build_reduced(X, tags, B, dt: int, Xred=None, row_stride: int | None = None, scales=None,

@@ -113,9 +113,9 @@ def test_host_validation_rejects_bad_arguments(lib):
     # FP32 (TF32 hi/lo): K padded to 128; Q 100 x 128 x 4 B and A 16 x 128 x 4 B, two copies each
     assert lib.glv_project_queries_workspace_size(100, 100, 2, 8, 0) == 2 * 51200 + 2 * 8192
 
-    tags = _ret_i32(lib, "glv_assign_tags", [P, i64, i32, P, i32, P, P])
-    assert tags(FAKE, 10, 8, FAKE, 0, FAKE, None) == INV
-    assert tags(FAKE, 10, 2048, FAKE, 4, FAKE, None) == 3          # D beyond the kernel's limit
+    tags = _ret_i32(lib, "glv_assign_tags", [P, i64, i32, P, i32, P, P, P])
+    assert tags(FAKE, 10, 8, FAKE, 0, FAKE, None, None) == INV
+    assert tags(FAKE, 10, 2048, FAKE, 4, FAKE, None, None) == 3          # D beyond the kernel's limit
 
     lib.glv_status_string.restype = ctypes.c_char_p
     assert lib.glv_status_string(2) == b"id or tag out of range"

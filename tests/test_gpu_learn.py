@@ -171,3 +171,57 @@ def test_refine_moves_towards_the_sphering_optimum(learn):
     assert np.isfinite(hist).all()
     assert l1 < 0.8 * l0, (l0, l1, l_opt)
     assert l1 > 0.97 * l_opt, (l0, l1, l_opt)
+
+
+# ---------------------------------------------------------------------------------------
+# spherical k-means (Appendix A)
+# ---------------------------------------------------------------------------------------
+
+def test_kmeans_update_vs_oracle(learn):
+    from paper_2410_22347_gb300 import glv
+    rng, Q, X, mu = _sets(31, 96, 10, 20000, 9)
+    X = X / np.linalg.norm(X, axis=1, keepdims=True)
+    tags = oracle.assign_tags(X, mu)
+    tags[tags == 4] = 3                      # cluster 4 empty: keeps its landmark
+    ref, counts = oracle.kmeans_update(X, tags, mu)
+    mu_t = _t(mu.astype(np.float32))
+    got, gc = glv.glv_kmeans_update(_t(X.astype(np.float32)), _t(tags), mu_t)
+    np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=2e-7)
+    np.testing.assert_array_equal(gc.cpu().numpy(), counts)
+    np.testing.assert_array_equal(got.cpu().numpy()[4], mu[4])
+
+
+def test_best_inner_product_output(learn):
+    from paper_2410_22347_gb300 import glv
+    rng, Q, X, mu = _sets(32, 64, 10, 5000, 12)
+    best = torch.empty(5000, dtype=torch.float32, device=dev())
+    tags = glv.glv_assign_tags(_t(X), _t(mu), best_ip=best).cpu().numpy()
+    ip = X.astype(np.float64) @ mu.astype(np.float64).T
+    np.testing.assert_allclose(best.cpu().numpy(), ip[np.arange(5000), tags], rtol=0,
+                               atol=1e-5 * np.abs(ip).max())
+    assert np.all(ip.max(axis=1) - ip[np.arange(5000), tags] <= 1e-5 * np.abs(ip).max())
+
+
+def test_spherical_kmeans_gpu_em_matches_oracle_em(learn):
+    """Same seeds: three GPU EM iterations reproduce the oracle's EM (tags agree away from
+    near-ties, landmarks to FP32 accuracy) and the objective does not decrease."""
+    from paper_2410_22347_gb300 import glv, kmeans
+    from paper_2410_22347_gb300 import synth
+    w = synth.make_workload(N=30000, D=64, d=8, C=6, nq=1, K_db=12, cands=1, kappa=0, k=1, cfg=87)
+    X = w.X.numpy()
+    mu0 = X[np.random.default_rng(0).choice(len(X), 6, replace=False)].copy()
+    mu_ref = mu0.copy()
+    mu_gpu = _t(mu0)
+    Xt = _t(X)
+    for _ in range(3):
+        tags_ref, margin = oracle.assign_tags(X, mu_ref, return_margin=True)
+        tags_gpu = glv.glv_assign_tags(Xt, mu_gpu).cpu().numpy()
+        sure = margin > 1e-5
+        np.testing.assert_array_equal(tags_gpu[sure], tags_ref[sure])
+        m64, _ = oracle.kmeans_update(X, tags_ref, mu_ref)
+        mu_ref = m64.astype(np.float32)
+        glv.glv_kmeans_update(Xt, _t(tags_ref), mu_gpu)   # same assignment on both sides
+        np.testing.assert_allclose(mu_gpu.cpu().numpy(), m64, atol=2e-7)
+    mu, hist = kmeans.spherical_kmeans(Xt, 6, iters=8, sample=0, seed=1)
+    assert all(b >= a - 1e-3 * abs(a) for a, b in zip(hist, hist[1:]))
+    np.testing.assert_allclose(np.linalg.norm(mu.cpu().numpy(), axis=1), 1.0, atol=1e-5)

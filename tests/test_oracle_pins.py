@@ -471,3 +471,49 @@ def test_pair_gradients_closed_form_and_fd():
             lm = oracle.pair_loss_grad(Q, X, tags, Am, Bm, qi.ravel(), xi.ravel(), want_grad=False)
             fd = (lp - lm) / (2 * h)
             assert abs(fd - G[c, r, k]) <= 1e-8 * max(1.0, abs(G[c, r, k]))
+
+
+# ---------------------------------------------------------------------------------------
+# spherical k-means (Appendix A)
+# ---------------------------------------------------------------------------------------
+
+def test_kmeans_update_against_segment_sums():
+    rng = _rng(50)
+    N, D, C = 700, 12, 6
+    X = _unit(rng, N, D)
+    tags = rng.integers(0, C - 1, N).astype(np.uint16)        # cluster C-1 stays empty
+    mu_in = _unit(rng, C, D)
+    mu, counts = oracle.kmeans_update(X, tags, mu_in)
+    sums = np.zeros((C, D))
+    np.add.at(sums, tags, X.astype(np.float64))
+    for c in range(C - 1):
+        np.testing.assert_allclose(mu[c], sums[c] / np.linalg.norm(sums[c]), rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(mu[C - 1], mu_in[C - 1].astype(np.float64))
+    np.testing.assert_array_equal(counts, np.bincount(tags, minlength=C))
+
+
+def test_kmeans_update_is_the_optimal_unit_landmark():
+    """For fixed assignments the normalised sum maximises sum_i <x_i, mu> over unit mu
+    (Cauchy-Schwarz), so no random unit vector does better."""
+    rng = _rng(51)
+    X = _unit(rng, 300, 8)
+    tags = np.zeros(300, np.uint16)
+    mu, _ = oracle.kmeans_update(X, tags, _unit(rng, 1, 8))
+    best = X.astype(np.float64).sum(0) @ mu[0]
+    trials = _unit(rng, 2000, 8).astype(np.float64) @ X.astype(np.float64).sum(0)
+    assert best >= trials.max() - 1e-12
+
+
+def test_spherical_kmeans_em_is_monotone():
+    rng = _rng(52)
+    X = _unit(rng, 2000, 16)
+    mu = X[rng.choice(2000, 7, replace=False)].copy()
+    prev = -np.inf
+    for _ in range(6):
+        tags = oracle.assign_tags(X, mu)
+        obj_e = oracle.spherical_objective(X, mu, tags)
+        assert obj_e >= prev - 1e-9
+        mu64, _ = oracle.kmeans_update(X, tags, mu)
+        mu = mu64.astype(np.float32)
+        prev = oracle.spherical_objective(X, mu, tags)
+        assert prev >= obj_e - 1e-4      # the M-step does not lower the objective
