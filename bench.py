@@ -674,6 +674,15 @@ def main():
         return run_reference(args)
     if args.workload == "refine-200k-d128":
         return run_learn(args)
+    if args.workload == "study-recall-vs-d":
+        import torch
+        from paper_2410_22347_gb300 import build_lib
+        build_lib.build()
+        from paper_2410_22347_gb300 import study
+        rows = study.recall_vs_d(torch.device("cuda", 0), **args.overrides)
+        print(json.dumps({"metric": "10-recall@10 of the reduced inner product (no re-rank) vs exact",
+                          "workload": "study-recall-vs-d", "data": "synthetic", "rows": rows}), flush=True)
+        return 0
     return run_glv(args)
 
 
