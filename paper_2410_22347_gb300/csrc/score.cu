@@ -67,10 +67,10 @@ void effective_score_config(int dt, int nch, int* G, int* mode) {
 }
 
 // Bulk gather needs its rings in shared memory; if they do not fit, use register loads.
-static ScoreConfig with_rings(ScoreConfig cfg, int C, int qstride, bool fused, int nch, int* RB) {
+static ScoreConfig with_rings(ScoreConfig cfg, int C, int qstride, bool fused, int nch, int kappa, int* RB) {
   *RB = 0;
   if (cfg.mode == 2) {
-    *RB = bulk_rows(C, qstride, fused, nch, kScoreSmemLimit);
+    *RB = bulk_rows(C, qstride, fused, nch, kappa, kScoreSmemLimit);
     if (*RB == 0) cfg.mode = 0;
   }
   return cfg;
@@ -87,7 +87,7 @@ cudaError_t launch_score(const ScoreArgs& a0, int dt, int64_t nq, int num_sms, c
   a.splits = splits;
   dim3 grid((unsigned)nq, (unsigned)splits);
   int RB = 0;
-  const ScoreConfig cfg = with_rings(resolve_config(dt, a.nch), a.C, a.qstride, false, a.nch, &RB);
+  const ScoreConfig cfg = with_rings(resolve_config(dt, a.nch), a.C, a.qstride, false, a.nch, 0, &RB);
   switch (dt) {
     case GLV_F32: return launch_score_dt<GLV_F32>(a, grid, RB, cfg, st);
     case GLV_BF16: return launch_score_dt<GLV_BF16>(a, grid, RB, cfg, st);
@@ -97,7 +97,7 @@ cudaError_t launch_score(const ScoreArgs& a0, int dt, int64_t nq, int num_sms, c
 
 size_t fused_smem_bytes(int C, int d, int dt) {
   const int eb = dt == GLV_F32 ? 4 : (dt == GLV_BF16 ? 2 : 1);
-  return score_smem(C, qstride_of(d, dt), true, 0, 0, (d * eb + 15) / 16).total();
+  return score_smem(C, qstride_of(d, dt), true, 0, 0, (d * eb + 15) / 16, GLV_MAX_KAPPA).total();
 }
 
 cudaError_t launch_score_topk(const ScoreArgs& a0, int dt, int64_t nq, int kappa, float* out_s,
@@ -113,7 +113,7 @@ cudaError_t launch_score_topk(const ScoreArgs& a0, int dt, int64_t nq, int kappa
   a.qstride = qstride_of(a.d, dt);
   a.splits = 1;
   int RB = 0;
-  const ScoreConfig cfg = with_rings(resolve_config(dt, a.nch), a.C, a.qstride, true, a.nch, &RB);
+  const ScoreConfig cfg = with_rings(resolve_config(dt, a.nch), a.C, a.qstride, true, a.nch, kappa, &RB);
   switch (dt) {
     case GLV_F32: return launch_fused_dt<GLV_F32>(a, nq, RB, kappa, out_s, out_id, cfg, st);
     case GLV_BF16: return launch_fused_dt<GLV_BF16>(a, nq, RB, kappa, out_s, out_id, cfg, st);

@@ -22,10 +22,13 @@ struct ScoreSmem {
   __host__ __device__ size_t total() const { return qs_bytes + keys_bytes + ring_bytes + bar_bytes; }
 };
 
-__host__ __device__ inline ScoreSmem score_smem(int C, int qstride, bool fused, int mode, int RB, int nch) {
+// keys_bytes (fused only): kFusedCache cached keys, then the kappa selected keys and ids,
+// rounded to 128 bytes so the rings stay aligned.
+__host__ __device__ inline ScoreSmem score_smem(int C, int qstride, bool fused, int mode, int RB, int nch,
+                                                int kappa = 0) {
   ScoreSmem m;
   m.qs_bytes = (((size_t)C * qstride * sizeof(float)) + 127) & ~size_t(127);
-  m.keys_bytes = fused ? (size_t)kFusedCache * sizeof(uint32_t) : 0;
+  m.keys_bytes = fused ? (((size_t)kFusedCache * sizeof(uint32_t) + (size_t)kappa * 8) + 127) & ~size_t(127) : 0;
   const int warps = kScoreThreads / 32;
   m.ring_bytes = mode == 2 ? (size_t)warps * kBulkSlots * RB * nch * 16 : 0;
   m.bar_bytes = mode == 2 ? (size_t)warps * kBulkSlots * sizeof(uint64_t) : 0;
@@ -33,11 +36,15 @@ __host__ __device__ inline ScoreSmem score_smem(int C, int qstride, bool fused, 
 }
 
 // Rows per bulk batch: the largest of 32, 16, 8 whose rings fit next to the rest.
-inline int bulk_rows(int C, int qstride, bool fused, int nch, size_t limit) {
+inline int bulk_rows(int C, int qstride, bool fused, int nch, int kappa, size_t limit) {
   for (int RB = 32; RB >= 8; RB /= 2)
-    if (score_smem(C, qstride, fused, 2, RB, nch).total() <= limit) return RB;
+    if (score_smem(C, qstride, fused, 2, RB, nch, kappa).total() <= limit) return RB;
   return 0;
 }
+
+#ifndef GLV_FUSED_MINB
+#define GLV_FUSED_MINB 6  // CTAs per SM the register-gather fused kernel is compiled for
+#endif
 
 template <int DT, int G, int NCH, int MODE, class Sink>
 GLV_DEV void score_span(const ScoreArgs& a, uint8_t* smem, const ScoreSmem& L, int RB, int64_t b0, int64_t b1,
@@ -96,14 +103,18 @@ __global__ void __launch_bounds__(kScoreThreads) score_kernel(const ScoreArgs a,
 // keys in shared memory and the radix selection runs there; a list longer than kFusedCache
 // spills its scores to the caller's scratch (L2-resident during the selection passes).
 template <int DT, int G, int NCH, int MODE>
-__global__ void __launch_bounds__(kScoreThreads, MODE == 1 ? 3 : (MODE == 2 ? 1 : 5))
+__global__ void __launch_bounds__(kScoreThreads, MODE == 1 ? 3 : (MODE == 2 ? 1 : GLV_FUSED_MINB))
     score_topk_kernel(const ScoreArgs a, int RB, int kappa, float* out_s, int32_t* out_id) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ TopkSmem S;
   __shared__ int abort_flag;
-  const ScoreSmem L = score_smem(a.C, a.qstride, true, MODE, RB, a.nch);
+  const ScoreSmem L = score_smem(a.C, a.qstride, true, MODE, RB, a.nch, kappa);
   uint32_t* kc = reinterpret_cast<uint32_t*>(smem + L.qs_bytes);
-  if (threadIdx.x == 0) abort_flag = 0;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    S.sel_key = kc + kFusedCache;
+    S.sel_id = reinterpret_cast<int32_t*>(kc + kFusedCache + kappa);
+  }
   init_bulk_bars<MODE>(smem, L);
   const int64_t j = blockIdx.x;
   stage_qp<DT>(a, j, reinterpret_cast<float*>(smem));
@@ -155,7 +166,7 @@ struct FusedLaunch {
   template <int DT, int G, int NCH, int MODE>
   cudaError_t go() {
     auto k = score_topk_kernel<DT, G, NCH, MODE>;
-    const size_t smem = score_smem(a.C, a.qstride, true, MODE, RB, a.nch).total();
+    const size_t smem = score_smem(a.C, a.qstride, true, MODE, RB, a.nch, kappa).total();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)nq, kScoreThreads, smem, st>>>(a, RB, kappa, out_s, out_id);

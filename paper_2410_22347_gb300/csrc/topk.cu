@@ -14,7 +14,11 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(const float* __restr
                                                            int kappa, float* __restrict__ out_s,
                                                            int32_t* __restrict__ out_id) {
   __shared__ TopkSmem S;
-  extern __shared__ uint32_t kcache[];
+  extern __shared__ uint32_t kcache[];  // kTopkCache keys, then kappa selected keys and ids
+  if (threadIdx.x == 0) {
+    S.sel_key = kcache + kTopkCache;
+    S.sel_id = reinterpret_cast<int32_t*>(kcache + kTopkCache + kappa);
+  }
   const int64_t j = blockIdx.x;
   const int64_t p0 = off[j];
   const int64_t L = off[j + 1] - p0;
@@ -31,7 +35,7 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(const float* __restr
 
 cudaError_t launch_topk(const float* scores, const int64_t* off, const int32_t* ids, int64_t nq,
                         int kappa, float* out_s, int32_t* out_id, cudaStream_t st) {
-  const size_t smem = (size_t)kTopkCache * sizeof(uint32_t);
+  const size_t smem = (size_t)kTopkCache * sizeof(uint32_t) + (size_t)kappa * 8;
   cudaError_t e = cudaFuncSetAttribute(topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -18,11 +18,13 @@ namespace glv {
 constexpr int kTopkThreads = 256;
 constexpr int kTopkCache = 8192;
 
+// Radix histogram and counters; the kappa selected (key, id) pairs live in caller-provided
+// shared memory (kappa entries each), so the footprint follows kappa.
 struct TopkSmem {
   uint32_t hist[256];
-  uint32_t sel_key[GLV_MAX_KAPPA];
-  int32_t sel_id[GLV_MAX_KAPPA];
   uint32_t bucket, above, count, n_eq;
+  uint32_t* sel_key;
+  int32_t* sel_id;
 };
 
 // After the histogram is complete: find the digit b whose bucket holds the `want`-th
