@@ -212,11 +212,11 @@ GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_
   }
 }
 
-// Lanes per candidate for a row of nch 16-byte chunks: the dtype's default group size when
-// that needs at most 8 loads per lane, else 32 lanes.
+// Default lanes per candidate per store type: 8 for FP32 and BF16 rows, 4 for FP8 rows (the
+// choices the autotuner made on every measured workload).
 template <int DT>
 constexpr int default_group() {
-  return (DT == GLV_F32) ? 8 : (DT == GLV_BF16 ? 4 : 2);
+  return (DT == GLV_F32) ? 8 : (DT == GLV_BF16 ? 8 : 4);
 }
 
 }  // namespace glv

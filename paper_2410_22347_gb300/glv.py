@@ -246,7 +246,7 @@ def glv_score_topk(Qp, Xred, row_stride: int, scales, dt: int, tags, off, ids, k
     return out_s, out_id
 
 
-SCORE_GROUPS = {GLV_F32: (4, 8, 16, 32), GLV_BF16: (2, 4, 8, 32), GLV_FP8_E4M3: (1, 2, 4, 32)}
+SCORE_GROUPS = {GLV_F32: (4, 8, 16, 32), GLV_BF16: (4, 8, 16, 32), GLV_FP8_E4M3: (2, 4, 8, 32)}
 
 
 GATHER_MODES = (0, 1, 2)  # registers, registers pipelined, bulk copies into shared memory
