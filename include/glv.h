@@ -191,6 +191,22 @@ glv_status glv_score_candidates(const float* Qp, int64_t nq, int32_t C, int32_t 
                                 float* scores, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Lazy candidate scoring, Algorithm 3: the same scores as glv_project_queries followed by
+ * glv_score_candidates (up to FP32 rounding of the projection), but the projected views
+ * q_c = A_c q are formed inside the scoring kernel, once per cluster that the query's list
+ * visits, instead of for all C clusters by a batched projection beforehand.
+ *   Q : nq x D float32 queries;  A : C x d x D float32;  other arguments as for
+ *   glv_score_candidates.   visited : nq int32 output (may be NULL) -- the number of
+ *   distinct clusters among each query's candidates.
+ * Limits: C * (d rounded up to 16 bytes + 4) + D floats must fit in shared memory.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_score_lazy(const float* Q, int64_t nq, int32_t D, const float* A, int32_t C,
+                          int32_t d, const void* Xred, int64_t row_stride, const float* scales,
+                          glv_dtype dt, const uint16_t* tags, int64_t N, const int64_t* cand_off,
+                          const int32_t* cand_ids, float* scores, int32_t* visited,
+                          int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Fused candidate scoring + top-kappa: the same computation and the same results (bit for
  * bit) as glv_score_candidates followed by glv_topk, without writing the scores to memory:
  * one CTA per query keeps them on chip and selects the kappa best there.

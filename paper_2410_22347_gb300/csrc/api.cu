@@ -42,12 +42,10 @@ static glv_status fill_score_args(ScoreArgs& a, const float* Qp, int64_t nq, int
   GLV_CHECK(aligned(Xred, 16), GLV_ERR_INVALID_ARG);
   GLV_CHECK(nq <= kMaxGridX, GLV_ERR_UNSUPPORTED);
   const int eb = elem_bytes(dt);
-  const int epc = 16 / eb;
-  const int64_t dpad = ((int64_t)d + epc - 1) / epc * epc;
-  GLV_CHECK((size_t)C * (dpad + 4) * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
   const int64_t bytes = (int64_t)d * eb;
   const int nch = (int)((bytes + 15) / 16);
   GLV_CHECK(nch <= 32 * 10, GLV_ERR_UNSUPPORTED);
+  GLV_CHECK((size_t)C * qp_qstride(nch, dt) * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
   a.Qp = Qp;
   a.C = C;
   a.d = d;
@@ -64,6 +62,7 @@ static glv_status fill_score_args(ScoreArgs& a, const float* Qp, int64_t nq, int
   a.nch = nch;
   a.tail = (int)(bytes - (int64_t)(nch - 1) * 16);
   a.splits = 1;
+  a.sbs = nch;
   return GLV_OK;
 }
 
@@ -183,6 +182,22 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
   GLV_CHECK(out_s && out_id, GLV_ERR_INVALID_ARG);
   GLV_CHECK(fused_smem_bytes(C, d, dt) <= kSmemLimit - 12 * 1024, GLV_ERR_UNSUPPORTED);  // + static TopkSmem
   GLV_LAUNCH(launch_score_topk(a, dt, nq, kappa, out_s, out_id, num_sms(), (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_score_lazy(const float* Q, int64_t nq, int32_t D, const float* A, int32_t C, int32_t d,
+                          const void* Xred, int64_t row_stride, const float* scales, glv_dtype dt,
+                          const uint16_t* tags, int64_t N, const int64_t* cand_off, const int32_t* cand_ids,
+                          float* scores, int32_t* visited, int32_t* d_status, void* stream) {
+  GLV_CHECK(D >= 1 && d <= D, GLV_ERR_INVALID_ARG);
+  ScoreArgs a;
+  const glv_status st = fill_score_args(a, Q /* placeholder, Qp unused */, nq, C, d, Xred, row_stride, scales, dt,
+                                        tags, N, cand_off, cand_ids, scores, d_status);
+  if (st != GLV_OK || nq == 0) return st;
+  GLV_CHECK(Q && A, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(lazy_smem_bytes(C, d, D, dt) <= kSmemLimit, GLV_ERR_UNSUPPORTED);
+  a.Qp = nullptr;
+  GLV_LAUNCH(launch_score_lazy(a, dt, nq, Q, D, A, visited, (cudaStream_t)stream));
   return GLV_OK;
 }
 

@@ -21,7 +21,26 @@ struct ScoreArgs {
   int nch;     // 16-byte chunks per row that hold data
   int tail;    // bytes of data in the last chunk (16 = full)
   int splits;  // CTAs per query (set by the launcher)
+  int sbs;     // float4 stride between the sub-blocks of a projected-query row (set by the launcher)
 };
+
+// Shared-memory layout of a projected-query row (see dot_chunk in score_dev.cuh): EPC/4
+// sub-blocks of sbs float4 each.  For BF16 and FP8 rows the sub-block stride is padded so that
+// the two candidates a quarter-warp serves read opposite halves of the banks (odd candidate
+// groups walk the sub-blocks in swapped order); rows then start on 128-byte boundaries.
+__host__ __device__ inline int qp_sub_blocks(int dt) { return dt == 0 ? 1 : (dt == 1 ? 2 : 4); }
+__host__ __device__ inline int qp_sbs(int nch, int dt) {
+  if (dt == 0) return nch;
+  int s = nch;
+  if (dt == 1)
+    while (s % 8 != 4) ++s;  // 16 * s = 64 (mod 128)
+  else
+    while (s % 4 != 2) ++s;  // 32 * s = 64 (mod 128)
+  return s;
+}
+__host__ __device__ inline int qp_qstride(int nch, int dt) {
+  return dt == 0 ? nch * 4 + 4 : qp_sub_blocks(dt) * qp_sbs(nch, dt) * 4;
+}
 
 struct RerankArgs {
   const float* X;
@@ -41,6 +60,9 @@ bool set_score_config(int dt, int G, int mode);
 void effective_score_config(int dt, int nch, int* G, int* mode);
 cudaError_t launch_score_topk(const ScoreArgs& a, int dt, int64_t nq, int kappa, float* out_s,
                               int32_t* out_id, int num_sms, cudaStream_t st);
+size_t lazy_smem_bytes(int C, int d, int D, int dt);
+cudaError_t launch_score_lazy(const ScoreArgs& a, int dt, int64_t nq, const float* Q, int D, const float* A,
+                              int32_t* visited, cudaStream_t st);
 cudaError_t launch_topk(const float* scores, const int64_t* off, const int32_t* ids, int64_t nq,
                         int kappa, float* out_s, int32_t* out_id, cudaStream_t st);
 cudaError_t launch_rerank(const RerankArgs& a, int64_t nq, bool vec, cudaStream_t st);

@@ -42,14 +42,13 @@ ScoreConfig get_score_config(int dt) {
   return g_cfg[dt];
 }
 
-static int epc_of(int dt) { return 16 / (dt == GLV_F32 ? 4 : (dt == GLV_BF16 ? 2 : 1)); }
-
-// qstride: floats per cluster row in shared memory; +4 (16 bytes) so consecutive cluster
-// rows start in different banks.
-static int qstride_of(int d, int dt) {
-  const int epc = epc_of(dt);
-  return (d + epc - 1) / epc * epc + 4;
+static int nch_of(int d, int dt) {
+  const int eb = dt == GLV_F32 ? 4 : (dt == GLV_BF16 ? 2 : 1);
+  return (d * eb + 15) / 16;
 }
+
+// qstride: floats per cluster row of the projected query in shared memory (qp_qstride).
+static int qstride_of(int d, int dt) { return qp_qstride(nch_of(d, dt), dt); }
 
 ScoreConfig resolve_config(int dt, int nch) {
   const ScoreConfig t = get_score_config(dt);
@@ -79,6 +78,7 @@ static ScoreConfig with_rings(ScoreConfig cfg, int C, int qstride, bool fused, i
 cudaError_t launch_score(const ScoreArgs& a0, int dt, int64_t nq, int num_sms, cudaStream_t st) {
   ScoreArgs a = a0;
   a.qstride = qstride_of(a.d, dt);
+  a.sbs = qp_sbs(a.nch, dt);
   // enough CTAs to fill the machine a few times over even for few queries
   const int64_t want = (int64_t)num_sms * 8;
   int splits = (int)((want + nq - 1) / nq);
@@ -111,6 +111,7 @@ cudaError_t launch_score_topk(const ScoreArgs& a0, int dt, int64_t nq, int kappa
   }
   ScoreArgs a = a0;
   a.qstride = qstride_of(a.d, dt);
+  a.sbs = qp_sbs(a.nch, dt);
   a.splits = 1;
   int RB = 0;
   const ScoreConfig cfg = with_rings(resolve_config(dt, a.nch), a.C, a.qstride, true, a.nch, kappa, &RB);

@@ -43,37 +43,47 @@ GLV_DEV float e4m3_hi_byte_scaled(uint32_t t) {
 
 // Dot product of one 16-byte chunk of a reduced row with the matching projected-query
 // elements.  The projected query of a cluster is laid out in shared memory as EPC/4
-// sub-blocks of float4, each sub-block holding the same 4-element slice of every chunk:
-// element (chunk ch, e) sits at float4 index (e / 4) * nch + ch.  Lanes that read
-// consecutive chunks of one row then read consecutive float4 words (no bank conflicts).
+// sub-blocks of float4 (stride sbs), each sub-block holding the same 4-element slice of every
+// chunk: element (chunk ch, e) sits at float4 index (e / 4) * sbs + ch.  Lanes that read
+// consecutive chunks of one row read consecutive float4 words.  When a quarter-warp serves two
+// candidates, the odd one (sw = 1) walks the sub-blocks in swapped order (BF16: 1,0; FP8:
+// 2,3,0,1), which with the padded sub-block stride puts the two candidates' reads 64 bytes
+// apart modulo 128 -- in opposite halves of the banks.  The FP32 sum follows the walk order,
+// so a candidate's result depends on the parity of its position in its group, which every
+// kernel derives from its offset in the candidate list.
 template <int DT>
-GLV_DEV float dot_chunk(uint4 v, const float* qrow, int ch, int nch) {
+GLV_DEV float dot_chunk(uint4 v, const float* qrow, int ch, int sbs, int sw) {
   const float4* q4 = reinterpret_cast<const float4*>(qrow);
   if constexpr (DT == GLV_F32) {
     float4 a = q4[ch];
     return a.x * __uint_as_float(v.x) + a.y * __uint_as_float(v.y) + a.z * __uint_as_float(v.z) +
            a.w * __uint_as_float(v.w);
   } else if constexpr (DT == GLV_BF16) {
-    float4 a = q4[ch], b = q4[nch + ch];
-    float s = a.x * __uint_as_float(v.x << 16);
-    s = fmaf(a.y, __uint_as_float(v.x & 0xffff0000u), s);
-    s = fmaf(a.z, __uint_as_float(v.y << 16), s);
-    s = fmaf(a.w, __uint_as_float(v.y & 0xffff0000u), s);
-    s = fmaf(b.x, __uint_as_float(v.z << 16), s);
-    s = fmaf(b.y, __uint_as_float(v.z & 0xffff0000u), s);
-    s = fmaf(b.z, __uint_as_float(v.w << 16), s);
-    s = fmaf(b.w, __uint_as_float(v.w & 0xffff0000u), s);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    float s = 0.f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int sb = t ^ sw;
+      const float4 a = q4[sb * sbs + ch];
+      const uint32_t lo = w[2 * sb], hi = w[2 * sb + 1];
+      s = fmaf(a.x, __uint_as_float(lo << 16), s);
+      s = fmaf(a.y, __uint_as_float(lo & 0xffff0000u), s);
+      s = fmaf(a.z, __uint_as_float(hi << 16), s);
+      s = fmaf(a.w, __uint_as_float(hi & 0xffff0000u), s);
+    }
     return s;
   } else {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
     float s = 0.f;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      float4 a = q4[t * nch + ch];
-      s = fmaf(a.x, e4m3_hi_byte_scaled(w[t] << 24), s);
-      s = fmaf(a.y, e4m3_hi_byte_scaled(w[t] << 16), s);
-      s = fmaf(a.z, e4m3_hi_byte_scaled(w[t] << 8), s);
-      s = fmaf(a.w, e4m3_hi_byte_scaled(w[t]), s);
+      const int sb = t ^ (sw << 1);
+      const float4 a = q4[sb * sbs + ch];
+      const uint32_t x = w[sb];
+      s = fmaf(a.x, e4m3_hi_byte_scaled(x << 24), s);
+      s = fmaf(a.y, e4m3_hi_byte_scaled(x << 16), s);
+      s = fmaf(a.z, e4m3_hi_byte_scaled(x << 8), s);
+      s = fmaf(a.w, e4m3_hi_byte_scaled(x), s);
     }
     return s;
   }
@@ -104,7 +114,7 @@ GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int c = t / dpad, r = t - c * dpad;
     const int ch = r / EPC, e = r - ch * EPC;
-    qs[c * a.qstride + ((e >> 2) * a.nch + ch) * 4 + (e & 3)] = (r < a.d) ? qj[(int64_t)c * a.d + r] : 0.f;
+    qs[c * a.qstride + ((e >> 2) * a.sbs + ch) * 4 + (e & 3)] = (r < a.d) ? qj[(int64_t)c * a.d + r] : 0.f;
   }
 }
 
@@ -139,7 +149,7 @@ GLV_DEV void load_row(const ScoreArgs& a, RowLoad<DT, G, NCH, PIPE>& r, int64_t 
 }
 
 template <int DT, int G, int NCH, bool PIPE, class Sink>
-GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, const float* qs, int gl,
+GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, const float* qs, int gl, int sw,
                         Sink& sink) {
   const bool ok = r.ok && r.tag < a.C;
   const float* qrow = qs + (ok ? r.tag : 0) * a.qstride;
@@ -150,7 +160,7 @@ GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, 
     if (ch < a.nch) {
       uint4 x = r.v[t];
       if (ch == a.nch - 1 && a.tail < 16) x = keep_bytes(x, a.tail);
-      acc += dot_chunk<DT>(x, qrow, ch, a.nch);
+      acc += dot_chunk<DT>(x, qrow, ch, a.sbs, sw);
     }
   }
 #pragma unroll
@@ -188,7 +198,7 @@ GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_
       id_next = (p + step < b1) ? (int64_t)__ldg(a.ids + p + step) : 0;
       RowLoad<DT, G, NCH, PIPE> r;
       load_row(a, r, p, b1, id, gl);
-      finish_row(a, r, qs, gl, sink);
+      finish_row(a, r, qs, gl, g & 1, sink);
     }
   } else {
     if (base >= b1) return;
@@ -206,7 +216,7 @@ GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_
         id_next = (pn + step < b1) ? (int64_t)__ldg(a.ids + pn + step) : 0;
         load_row(a, nxt, pn, b1, id, gl);
       }
-      finish_row(a, cur, qs, gl, sink);
+      finish_row(a, cur, qs, gl, g & 1, sink);
       cur = nxt;
     }
   }

@@ -89,4 +89,14 @@ ScoreConfig effective_config(int nch, int tuned_G, int tuned_mode) {
   return {32, 0};
 }
 
+// The library-default configuration only (register gather), for kernels that are not tuned.
+template <int DT, class F>
+cudaError_t dispatch_score_default(int nch, F& f) {
+  const ScoreConfig c = effective_config<DT>(nch, 0, 0);
+  const int n = round_nch((nch + c.G - 1) / c.G, 0);
+  if (c.G == Groups<DT>::G0) return dispatch_nch_mode<DT, Groups<DT>::G0, 0>(n, f);
+  if (c.G == Groups<DT>::kHi) return dispatch_nch_mode<DT, Groups<DT>::kHi, 0>(n, f);
+  return dispatch_nch_mode<DT, 32, 0>(n, f);
+}
+
 }  // namespace glv

@@ -87,8 +87,10 @@ __global__ void __launch_bounds__(kScoreThreads) score_kernel(const ScoreArgs a,
   stage_qp<DT>(a, j, reinterpret_cast<float*>(smem));
   __syncthreads();
   const int64_t p0 = a.off[j], p1 = a.off[j + 1];
-  const int64_t per = (p1 - p0 + a.splits - 1) / a.splits;
-  const int64_t b0 = p0 + (int64_t)blockIdx.y * per;
+  // split boundaries on multiples of 64 candidates: every candidate keeps the position parity
+  // (and so the summation order, see dot_chunk) it has in the fused kernel
+  const int64_t per = ((p1 - p0 + a.splits - 1) / a.splits + 63) / 64 * 64;
+  const int64_t b0 = min(p1, p0 + (int64_t)blockIdx.y * per);
   const int64_t b1 = min(p1, b0 + per);
   float* scores = a.scores;
   auto sink = [scores](int64_t p, float s) { scores[p] = s; };

@@ -50,6 +50,7 @@ def _load() -> ctypes.CDLL:
         "glv_score_candidates": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P]),
         "glv_score_topk": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, i32, P, P, P, P, P]),
         "glv_topk": (i32, [P, P, P, i64, i32, P, P, P]),
+        "glv_score_lazy": (i32, [P, i64, i32, P, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P, P]),
         "glv_set_score_config": (i32, [i32, i32, i32]),
         "glv_get_score_config": (i32, [i32, i32, P, P]),
         "glv_rerank": (i32, [P, i64, i32, P, i64, P, i32, i32, P, P, P, P]),
@@ -221,6 +222,27 @@ def glv_score_candidates(Qp, Xred, row_stride: int, scales, dt: int, tags, off, 
                                      _ptr(tags), N, _ptr(off), _ptr(ids), _ptr(scores),
                                      _ptr(d_status), _stream(stream)))
     return scores
+
+
+def glv_score_lazy(Q, A, Xred, row_stride: int, scales, dt: int, tags, off, ids, scores=None, visited=None,
+                   d_status=None, stream=None):
+    """Algorithm 3 (lazy): scores with q_c = A_c q formed per visited cluster inside the
+    kernel.  Returns (scores, visited-cluster count per query)."""
+    _need(Q, torch.float32, "Q", 2)
+    _need(A, torch.float32, "A", 3)
+    _need(tags, torch.uint16, "tags", 1)
+    _need(off, torch.int64, "cand_off", 1)
+    _need(ids, torch.int32, "cand_ids", 1)
+    nq, D = Q.shape
+    C, d, _ = A.shape
+    if scores is None:
+        scores = torch.empty(max(ids.shape[0], 1), dtype=torch.float32, device=Q.device)
+    if visited is None:
+        visited = torch.empty(nq, dtype=torch.int32, device=Q.device)
+    _check("glv_score_lazy", _lib.glv_score_lazy(_ptr(Q), nq, D, _ptr(A), C, d, _ptr(Xred), row_stride, _ptr(scales),
+                                                 dt, _ptr(tags), tags.shape[0], _ptr(off), _ptr(ids), _ptr(scores),
+                                                 _ptr(visited), _ptr(d_status), _stream(stream)))
+    return scores, visited
 
 
 def glv_score_topk(Qp, Xred, row_stride: int, scales, dt: int, tags, off, ids, kappa: int, scores_scratch=None,

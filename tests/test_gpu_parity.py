@@ -501,13 +501,14 @@ def test_every_score_configuration_matches_oracle(glv, dt_name):
 
 
 @pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
-@pytest.mark.parametrize("mode", [1, 2])
-def test_fused_matches_separate_in_every_gather_mode(glv, dt_name, mode):
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("gi", [0, 1])
+def test_fused_matches_separate_in_every_gather_mode(glv, dt_name, mode, gi):
     """Gather modes change only how rows travel; the scores (and so the selections) of the
-    fused and the stand-alone paths stay bit-identical."""
+    fused and the stand-alone (split) paths stay bit-identical for every group size."""
     dt = glv.DTYPES[dt_name]
     try:
-        glv.glv_set_score_config(dt, glv.SCORE_GROUPS[dt][1], mode)
+        glv.glv_set_score_config(dt, glv.SCORE_GROUPS[dt][gi], mode)
         test_score_topk_fused_matches_separate(glv, dt_name, 700, 100)
     finally:
         glv.glv_set_score_config(dt, 0, 0)
@@ -528,3 +529,39 @@ def test_score_config_roundtrip(glv):
             glv.glv_set_score_config(glv.GLV_BF16, 4, 3)
     finally:
         glv.glv_set_score_config(glv.GLV_BF16, 0, 0)
+
+
+# ---------------------------------------------------------------------------------------
+# lazy inner product (Algorithm 3) against the eager path and the oracle
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
+def test_score_lazy_matches_oracle_and_counts_visited_clusters(glv, dt_name):
+    dt = glv.DTYPES[dt_name]
+    rng, X, Q, mu, A, B, tags = _problem(77, N=4000, D=96, d=40, C=9, nq=30)
+    lens = [0, 1, 5, 64, 700, 2000] + [50] * 24
+    lists = _ragged_lists(rng, 30, len(X), lens)
+    off, ids = _csr(lists)
+    Xred, scales = glv.glv_build_reduced(_t(X), _t(tags), _t(B), dt)
+    rs = glv.min_row_stride(40, dt)
+    st = _status()
+    got, visited = glv.glv_score_lazy(_t(Q), _t(A), Xred, rs, scales, dt, _t(tags), _t(off), _t(ids), d_status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    # visited-cluster counts are exact
+    want_vis = [len(set(tags[l].tolist())) for l in lists]
+    np.testing.assert_array_equal(visited.cpu().numpy(), want_vis)
+    # scores: the oracle on the store's own decoded rows with the exact projection
+    Xr = oracle.build_reduced(X, tags, B)
+    if dt == glv.GLV_F32:
+        xr_used = Xred.cpu().numpy().view(np.float32)[:, :40].astype(np.float64)
+    elif dt == glv.GLV_BF16:
+        xr_used = oracle.bf16_decode(Xred.cpu().numpy().view(np.uint16)[:, :40])
+    else:
+        xr_used = oracle.dequantize_fp8_rows(Xred.cpu().numpy()[:, :40], scales.cpu().numpy())
+    Qp = oracle.project(Q, A)
+    ref, _ = oracle.score(Qp, xr_used, tags, off, ids)
+    cand_j = np.repeat(np.arange(30), np.diff(off))
+    scale = np.linalg.norm(Qp, axis=2)[cand_j, tags[ids]] * np.linalg.norm(xr_used, axis=1)[ids]
+    ok, worst, bad = scores_close(got.cpu().numpy()[:len(ids)], ref, scale, TOL)
+    assert ok, worst
