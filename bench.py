@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true", help="keep the library's default scoring configuration")
     p.add_argument("--graph", action="store_true", help="time the step as a captured CUDA graph")
     p.add_argument("--queries", default="ood", choices=["ood", "id"], help="query distribution")
+    p.add_argument("--lazy", action="store_true",
+                   help="also time the lazy inner product (Algorithm 3) against the eager path")
     p.add_argument("--score-error", action="store_true",
                    help="report each store's score error against the FP64 oracle on the recall sample")
     p.add_argument("--per-query", type=int, default=0,
@@ -175,8 +177,9 @@ def source_sha(*rel):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = ("paper_2410_22347_gb300/csrc/fused.cu", "paper_2410_22347_gb300/csrc/score_dev.cuh",
-                  "paper_2410_22347_gb300/csrc/topk_dev.cuh", "paper_2410_22347_gb300/csrc/common.cuh")
+KERNEL_SOURCES = tuple("paper_2410_22347_gb300/csrc/" + f for f in (
+    "score_variants.cuh", "score_dev.cuh", "score_launch.cuh", "score_bulk.cuh", "topk_dev.cuh", "common.cuh",
+    "kernels.cuh", "score.cu", "score_bf16_fused.cu", "score_fp8_fused.cu", "score_f32_fused.cu"))
 
 
 def recorded_traffic(workload: str, store: str):
@@ -442,6 +445,41 @@ def run_glv(args):
             batching["per_query_launches"] = {"queries": nsub, "ms": pms,
                                               "value": job_throughput(nsub, world, pms)}
 
+    # ---- lazy (Algorithm 3) vs eager (Algorithm 4) scoring + top-kappa ----
+    lazy = None
+    if args.lazy:
+        ix = idx[args.store]
+        b = ix._buffers(nq, total, w.kappa, w.k)
+        vis = torch.empty(nq, dtype=torch.int32, device=dev)
+
+        def lazy_step():
+            glv.glv_score_lazy(w.Q, ix.A, ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids,
+                               scores=b["scores"], visited=vis)
+            glv.glv_topk(b["scores"], w.off, w.ids, w.kappa, out_s=b["ts"], out_id=b["ti"])
+
+        def eager_step():
+            glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"])
+            glv.glv_score_topk(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids, w.kappa,
+                               scores_scratch=b["scores"], out_s=b["ts"], out_id=b["ti"])
+
+        def timed(fn, reps=10):
+            fn()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return sum(ms) / len(ms)
+        le, ee = timed(lazy_step), timed(eager_step)
+        v = vis.float()
+        lazy = {"lazy_ms": le, "eager_ms": ee, "visited_clusters_mean": float(v.mean()),
+                "visited_clusters_max": int(vis.max()), "clusters": C}
+
     # ---- end-to-end through the public host API (pinned host buffers, copies timed) ----
     ix = idx[args.store]
     Qh = w.Q.cpu().pin_memory()
@@ -567,6 +605,7 @@ def run_glv(args):
                   for st, r in results.items()},
         "autotune": tuned or None,
         "batching": batching or None,
+        "lazy_vs_eager": lazy,
     }
     line.update(line_extra)
     if rec is not None and rec < 0.9:

@@ -75,7 +75,7 @@ int64_t glv_min_row_stride(int32_t d, glv_dtype dt);
  *   tags    : N uint16 output.  Ties go to the lowest c.  FP32 accumulation.
  *   best_ip : N float32 output <x_i, mu_{c_i}> (may be NULL) -- the spherical k-means
  *             objective terms (Appendix A) and the k-means++ seeding weights.
- * Limits: D <= 1024 and C * D * 4 bytes must fit in shared memory (C * D <= 58112).
+ * Limits: D <= 1024 (else GLV_ERR_UNSUPPORTED); any C <= 65536.
  * ------------------------------------------------------------------------------------- */
 glv_status glv_assign_tags(const float* X, int64_t N, int32_t D, const float* mu, int32_t C,
                            uint16_t* tags, float* best_ip, void* stream);

@@ -100,7 +100,7 @@ glv_status glv_assign_tags(const float* X, int64_t N, int32_t D, const float* mu
   GLV_CHECK(N >= 0 && D >= 1 && C >= 1 && C <= 65536, GLV_ERR_INVALID_ARG);
   if (N == 0) return GLV_OK;
   GLV_CHECK(X && mu && tags, GLV_ERR_INVALID_ARG);
-  GLV_CHECK(D <= 1024 && (size_t)C * D * 4 <= kSmemLimit, GLV_ERR_UNSUPPORTED);
+  GLV_CHECK(D <= 1024, GLV_ERR_UNSUPPORTED);
   GLV_LAUNCH(launch_tags(X, N, D, mu, C, tags, best_ip, num_sms(), (cudaStream_t)stream));
   return GLV_OK;
 }

@@ -58,32 +58,37 @@ GLV_DEV float dot_chunk(uint4 v, const float* qrow, int ch, int sbs, int sw) {
     float4 a = q4[ch];
     return a.x * __uint_as_float(v.x) + a.y * __uint_as_float(v.y) + a.z * __uint_as_float(v.z) +
            a.w * __uint_as_float(v.w);
-  } else if constexpr (DT == GLV_BF16) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    float s = 0.f;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int sb = t ^ sw;
-      const float4 a = q4[sb * sbs + ch];
-      const uint32_t lo = w[2 * sb], hi = w[2 * sb + 1];
-      s = fmaf(a.x, __uint_as_float(lo << 16), s);
-      s = fmaf(a.y, __uint_as_float(lo & 0xffff0000u), s);
-      s = fmaf(a.z, __uint_as_float(hi << 16), s);
-      s = fmaf(a.w, __uint_as_float(hi & 0xffff0000u), s);
-    }
-    return s;
   } else {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    // odd lane groups walk the two halves of the chunk in swapped order; the words are picked
+    // with selects (a runtime index into a register array would put it in local memory)
+    const uint32_t x0 = sw ? v.z : v.x, x1 = sw ? v.w : v.y;
+    const uint32_t x2 = sw ? v.x : v.z, x3 = sw ? v.y : v.w;
+    const float4* qa = q4 + sw * sbs + ch;
+    const float4* qb = q4 + (sw ^ 1) * sbs + ch;
     float s = 0.f;
+    if constexpr (DT == GLV_BF16) {
+      // sub-block 0 holds elements 0..3 (words 0, 1), sub-block 1 elements 4..7 (words 2, 3)
+      const float4 a = *qa, b = *qb;
+      s = fmaf(a.x, __uint_as_float(x0 << 16), s);
+      s = fmaf(a.y, __uint_as_float(x0 & 0xffff0000u), s);
+      s = fmaf(a.z, __uint_as_float(x1 << 16), s);
+      s = fmaf(a.w, __uint_as_float(x1 & 0xffff0000u), s);
+      s = fmaf(b.x, __uint_as_float(x2 << 16), s);
+      s = fmaf(b.y, __uint_as_float(x2 & 0xffff0000u), s);
+      s = fmaf(b.z, __uint_as_float(x3 << 16), s);
+      s = fmaf(b.w, __uint_as_float(x3 & 0xffff0000u), s);
+    } else {
+      // sub-block t holds the four bytes of word t; odd groups take them in the order 2, 3, 0, 1
+      const uint32_t xs[4] = {x0, x1, x2, x3};
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int sb = t ^ (sw << 1);
-      const float4 a = q4[sb * sbs + ch];
-      const uint32_t x = w[sb];
-      s = fmaf(a.x, e4m3_hi_byte_scaled(x << 24), s);
-      s = fmaf(a.y, e4m3_hi_byte_scaled(x << 16), s);
-      s = fmaf(a.z, e4m3_hi_byte_scaled(x << 8), s);
-      s = fmaf(a.w, e4m3_hi_byte_scaled(x), s);
+      for (int t = 0; t < 4; ++t) {
+        const float4 a = q4[(t ^ (sw << 1)) * sbs + ch];
+        const uint32_t x = xs[t];
+        s = fmaf(a.x, e4m3_hi_byte_scaled(x << 24), s);
+        s = fmaf(a.y, e4m3_hi_byte_scaled(x << 16), s);
+        s = fmaf(a.z, e4m3_hi_byte_scaled(x << 8), s);
+        s = fmaf(a.w, e4m3_hi_byte_scaled(x), s);
+      }
     }
     return s;
   }
@@ -100,8 +105,6 @@ GLV_DEV uint4 keep_bytes(uint4 v, int nbytes) {
   }
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
-
-
 
 // Stage the C projected views of query j into shared memory in the sub-block layout of
 // dot_chunk (rows of a.qstride floats; elements d..dpad-1 are zero).

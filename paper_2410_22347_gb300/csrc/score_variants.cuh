@@ -46,6 +46,15 @@ inline int bulk_rows(int C, int qstride, bool fused, int nch, int kappa, size_t 
 #define GLV_FUSED_MINB 6  // CTAs per SM the register-gather fused kernel is compiled for
 #endif
 
+constexpr int fused_min_blocks_regs(int n) { return n <= 4 ? GLV_FUSED_MINB : n <= 5 ? 5 : n <= 8 ? 4 : 3; }
+
+// CTAs per SM the fused kernel is compiled for: the register budget must hold NCH row chunks
+// per lane (x2 when the next candidate's loads are in flight, mode 1) without spilling; the
+// FP8 decode costs about one chunk's worth of registers more.
+constexpr int fused_min_blocks(int dt, int mode, int nch) {
+  return mode == 2 ? 1 : mode == 1 ? 3 : fused_min_blocks_regs(nch + (dt == GLV_FP8_E4M3 ? 1 : 0));
+}
+
 template <int DT, int G, int NCH, int MODE, class Sink>
 GLV_DEV void score_span(const ScoreArgs& a, uint8_t* smem, const ScoreSmem& L, int RB, int64_t b0, int64_t b1,
                         Sink& sink, volatile int* abort) {
@@ -105,7 +114,7 @@ __global__ void __launch_bounds__(kScoreThreads) score_kernel(const ScoreArgs a,
 // keys in shared memory and the radix selection runs there; a list longer than kFusedCache
 // spills its scores to the caller's scratch (L2-resident during the selection passes).
 template <int DT, int G, int NCH, int MODE>
-__global__ void __launch_bounds__(kScoreThreads, MODE == 1 ? 3 : (MODE == 2 ? 1 : GLV_FUSED_MINB))
+__global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH))
     score_topk_kernel(const ScoreArgs a, int RB, int kappa, float* out_s, int32_t* out_id) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ TopkSmem S;

@@ -1,6 +1,7 @@
 // tags.cu -- cluster tags of Eq. (cluster_tag), Section 4:  c_i = argmax_c <x_i, mu_c>.
 //
-// The C landmarks are staged once per CTA in shared memory.  One warp per database row:
+// The C landmarks are staged in shared memory (once per CTA when they fit in 96 KB, else in
+// tiles of whole landmarks, re-read from L2 for every group of rows).  One warp per database row:
 // lane l holds elements l, l+32, ... of the row in registers (a coalesced read of the
 // row), and for each landmark the warp forms the dot with an xor-shuffle reduction, which
 // leaves the full sum in every lane.  Ties keep the lowest c (strict comparison).
@@ -11,47 +12,69 @@ namespace glv {
 
 template <int NPL>  // row elements per lane (D <= 32 * NPL)
 __global__ void __launch_bounds__(256) tags_kernel(const float* __restrict__ X, int64_t N, int D,
-                                                   const float* __restrict__ mu, int C,
+                                                   const float* __restrict__ mu, int C, int tile_c,
                                                    uint16_t* __restrict__ tags, float* __restrict__ best_ip) {
-  extern __shared__ float ms[];  // C x D
-  for (int t = threadIdx.x; t < C * D; t += blockDim.x) ms[t] = mu[t];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < N;
-       i += warps) {
+  // landmarks are staged tile_c at a time (all of them at once when they fit); a warp keeps its
+  // row in registers across the tiles, and the tiles are visited in cluster order so the
+  // running argmax keeps the first maximum
+  extern __shared__ float ms[];  // tile_c x D
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const bool single = tile_c >= C;
+  if (single) {
+    for (int t = threadIdx.x; t < C * D; t += blockDim.x) ms[t] = mu[t];
+    __syncthreads();
+  }
+  // block-uniform loop over groups of wpb rows (the tile loop below synchronises the block)
+  for (int64_t i0 = (int64_t)blockIdx.x * wpb; i0 < N; i0 += (int64_t)gridDim.x * wpb) {
+    const int64_t i = i0 + warp;
+    const bool row = i < N;
     float x[NPL];
 #pragma unroll
     for (int u = 0; u < NPL; ++u) {
       const int e = lane + 32 * u;
-      x[u] = e < D ? ld_stream_f32(X + i * D + e) : 0.f;
+      x[u] = (row && e < D) ? ld_stream_f32(X + i * D + e) : 0.f;
     }
     float best = -INFINITY;
     int bc = 0;
-    for (int c = 0; c < C; ++c) {
-      const float* m = ms + c * D;
-      float s = 0.f;
-#pragma unroll
-      for (int u = 0; u < NPL; ++u) {
-        const int e = lane + 32 * u;
-        if (e < D) s = fmaf(x[u], m[e], s);
+    for (int c0 = 0; c0 < C; c0 += tile_c) {
+      const int nc = min(tile_c, C - c0);
+      if (!single) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nc * D; t += blockDim.x) ms[t] = mu[(int64_t)c0 * D + t];
+        __syncthreads();
       }
-      s = warp_sum(s);
-      if (s > best) {
-        best = s;
-        bc = c;
+      for (int c = 0; c < nc; ++c) {
+        const float* m = ms + c * D;
+        float s = 0.f;
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          const int e = lane + 32 * u;
+          if (e < D) s = fmaf(x[u], m[e], s);
+        }
+        s = warp_sum(s);
+        if (s > best) {
+          best = s;
+          bc = c0 + c;
+        }
       }
     }
-    if (lane == 0) {
+    if (row && lane == 0) {
       tags[i] = (uint16_t)bc;
       if (best_ip) best_ip[i] = best;
     }
   }
 }
 
+// Landmark tile: as many whole landmarks as fit in 96 KB of shared memory (two CTAs per SM).
+inline int tags_tile(int C, int D) {
+  const int fit = (96 * 1024) / (D * 4);
+  return fit < 1 ? 1 : (fit < C ? fit : C);
+}
+
 cudaError_t launch_tags(const float* X, int64_t N, int D, const float* mu, int C, uint16_t* tags,
                         float* best_ip, int num_sms, cudaStream_t st) {
-  const size_t smem = (size_t)C * D * sizeof(float);
+  const int tile_c = tags_tile(C, D);
+  const size_t smem = (size_t)tile_c * D * sizeof(float);
   int64_t blocks = (N + 7) / 8;
   const int64_t cap = (int64_t)num_sms * 8;
   if (blocks > cap) blocks = cap;
@@ -61,7 +84,7 @@ cudaError_t launch_tags(const float* X, int64_t N, int D, const float* mu, int C
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                          (int)smem);                                     \
     if (e != cudaSuccess) return e;                                                      \
-    k<<<(unsigned)blocks, 256, smem, st>>>(X, N, D, mu, C, tags, best_ip);               \
+    k<<<(unsigned)blocks, 256, smem, st>>>(X, N, D, mu, C, tile_c, tags, best_ip);       \
     return cudaGetLastError();                                                           \
   }
   const int npl = (D + 31) / 32;

@@ -79,13 +79,18 @@ def _problem(seed, N=3000, D=96, d=27, C=5, nq=23, orth=True):
 # Eq. (cluster_tag)
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("N,D,C", [(5000, 96, 7), (1000, 768, 32), (777, 33, 1), (300, 1024, 40)])
+# (300, 1024, 40), (2000, 768, 130) and (3000, 128, 1000) stage the landmarks in several
+# shared-memory tiles (ragged last tile); the tie 40 = 2 straddles a tile boundary
+@pytest.mark.parametrize("N,D,C", [(5000, 96, 7), (1000, 768, 32), (777, 33, 1), (300, 1024, 40),
+                                   (2000, 768, 130), (3000, 128, 1000)])
 def test_assign_tags(glv, N, D, C):
     rng = _rng(N + D + C)
     X = _unit(rng, N, D)
     mu = _unit(rng, C, D)
     if C > 3:
         mu[3] = mu[1]  # exact ties: the lower index must win
+    if C > 40:
+        mu[40] = mu[2]
     ref, margin = oracle.assign_tags(X, mu, return_margin=True)
     got = glv.glv_assign_tags(_t(X), _t(mu)).cpu().numpy()
     sure = margin > 1e-5
@@ -96,6 +101,8 @@ def test_assign_tags(glv, N, D, C):
     assert np.all(best - ip[np.arange(N), got] <= 1e-5)
     if C > 3:
         assert not np.any(got == 3)
+    if C > 40:
+        assert not np.any(got == 40)
 
 
 # ---------------------------------------------------------------------------------------
