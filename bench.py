@@ -362,9 +362,11 @@ def run_glv(args):
         if sampler:
             sampler.__enter__()
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push(f"timed_{st}")  # lets a profiler select the timed launches
         for s in range(args.steps):
             flush.zero_()  # evict L2 between timed steps (not inside the timed events)
             step(ix, evs[s])
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         if sampler:
