@@ -58,7 +58,7 @@ typedef enum {
  *                  the represented value is s_i * decode(code_ij). */
 typedef enum { GLV_F32 = 0, GLV_BF16 = 1, GLV_FP8_E4M3 = 2 } glv_dtype;
 
-#define GLV_ABI_VERSION 1
+#define GLV_ABI_VERSION 2
 #define GLV_MAX_KAPPA 1024 /* largest kappa accepted by glv_topk / glv_rerank */
 
 int32_t glv_abi_version(void);
@@ -231,13 +231,33 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
  * only where the rings fit in shared memory, else mode 0).  The choice changes only speed
  * and the order in which a row's partial dots are summed (FP32 rounding); the gather mode
  * does not change that order, and glv_score_candidates and glv_score_topk always use the
- * same configuration, so their results stay identical.  A choice that cannot serve a row
- * width falls back to the default for that width; glv_get_score_config reports the
- * configuration used for rows of width d.  Process-wide setting.
+ * same configuration, so their results stay identical.  smem_carveout_kb caps the shared-
+ * memory part of the SM's shared-memory / L1 split for the scoring kernels (0 = the
+ * driver's choice, else 16..256 KB; ignored where one CTA would not fit under the cap): the
+ * driver sizes that split for the kernel's full occupancy, and the L1 left over stages the
+ * gathered rows in flight, so fewer CTAs with more L1 can be faster.  It changes only speed.
+ * A choice that cannot serve a row width falls back to the default for that width;
+ * glv_get_score_config reports the configuration used for rows of width d.  Process-wide
+ * setting.  Errors: GLV_ERR_INVALID_ARG for an unknown dt, lane count, mode or carveout.
  * ------------------------------------------------------------------------------------- */
-glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t gather_mode);
+glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t gather_mode,
+                                int32_t smem_carveout_kb);
 glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate,
-                                int32_t* gather_mode);
+                                int32_t* gather_mode, int32_t* smem_carveout_kb);
+
+/* ---------------------------------------------------------------------------------------
+ * Gather calibration (no counterpart in the paper; a measuring instrument for the roofline
+ * of the gather-score): for every entry p of ids, reads the whole row ids[p] of a row-major
+ * store and writes out[p] = the row's 32-bit words summed as floats -- the same bytes in the
+ * same random order as the scoring kernels read, without their arithmetic, so its bandwidth
+ * is the practical ceiling of random row gathers of that width on this GPU.
+ *   rows      : n_rows x row_bytes device bytes, 16-byte aligned; row_bytes a multiple of
+ *               16, at most 1024 (else GLV_ERR_UNSUPPORTED).
+ *   ids       : n_ids int32 row ids; an id outside [0, n_rows) writes 0 and sets
+ *               GLV_ERR_BAD_ID in d_status (optional).   out : n_ids float32.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_gather_rows(const void* rows, int64_t row_bytes, int64_t n_rows, const int32_t* ids,
+                           int64_t n_ids, float* out, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Per-query top-kappa of the scores (Algorithm 1: the main step hands kappa candidates to

@@ -2,7 +2,8 @@
 
 The scoring kernels are instantiated for several lanes-per-candidate group sizes and three
 row-gather modes (register loads, pipelined register loads, bulk copies into shared memory;
-see csrc/score_launch.cuh).  Which one keeps
+see csrc/score_launch.cuh), and each launch may cap the SM's shared-memory carveout (fewer
+CTAs, more L1 for the rows in flight).  Which combination keeps
 HBM busiest depends on the row width, the store type, the candidate-list lengths and the
 GPU, so ``tune_score`` times every offered configuration of the fused score + top-kappa
 call on the caller's own workload (CUDA events on the launching stream, L2 evicted between
@@ -23,7 +24,7 @@ CACHE = os.environ.get("GLV_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"
 
 def _key(dt: int, d: int, C: int, mean_len: float) -> str:
     name = torch.cuda.get_device_name()
-    return f"{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
+    return f"v2|{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
 
 
 def _load_cache() -> dict:
@@ -48,27 +49,29 @@ def _save_cache(c: dict) -> None:
 def configurations(dt: int):
     for G in glv.SCORE_GROUPS[dt]:
         for mode in glv.GATHER_MODES:
-            yield G, mode
+            for carve in glv.SCORE_CARVEOUTS:
+                yield G, mode, carve
 
 
 def tune_score(index, Q, off, ids, kappa: int, reps: int = 5, use_cache: bool = True, verbose: bool = False):
     """Pick the fastest scoring configuration for ``index``'s store on this workload.
-    Returns (G, gather_mode, table) where table maps "G/mode" to the mean ms per call."""
+    Returns (G, gather_mode, carveout_kb, table) where table maps "G/mode/carveout" to the
+    mean ms per call."""
     nq = Q.shape[0]
     mean_len = ids.shape[0] / max(nq, 1)
-    key = _key(index.dt, index.d, index.C, mean_len)
+    key = _key(index.dt, index.d, index.C, mean_len) + f"|k{kappa}"
     cache = _load_cache() if use_cache else {}
     if key in cache:
-        G, mode = cache[key]["G"], cache[key]["mode"]
-        glv.glv_set_score_config(index.dt, G, mode)
-        return G, mode, cache[key].get("table", {})
+        G, mode, carve = cache[key]["G"], cache[key]["mode"], cache[key].get("carve", 0)
+        glv.glv_set_score_config(index.dt, G, mode, carve)
+        return G, mode, carve, cache[key].get("table", {})
     b = index._buffers(nq, ids.shape[0], kappa, kappa)
     glv.glv_project_queries(Q, index.A, index.compute, Qp=b["Qp"], workspace=b["pws"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=Q.device)  # 256 MB > L2
     table = {}
     seen = set()
-    for G, mode in configurations(index.dt):
-        glv.glv_set_score_config(index.dt, G, mode)
+    for G, mode, carve in configurations(index.dt):
+        glv.glv_set_score_config(index.dt, G, mode, carve)
         eff = glv.glv_get_score_config(index.dt, index.d)
         if eff in seen:  # this choice cannot serve the row width; it maps onto one already timed
             continue
@@ -88,13 +91,13 @@ def tune_score(index, Q, off, ids, kappa: int, reps: int = 5, use_cache: bool = 
             e1.record()
             e1.synchronize()
             ms += e0.elapsed_time(e1)
-        table[f"{eff[0]}/{int(eff[1])}"] = ms / reps
+        table[f"{eff[0]}/{eff[1]}/{eff[2]}"] = ms / reps
         if verbose:
-            print(f"  score config G={eff[0]:2d} mode={int(eff[1])}: {ms / reps:.3f} ms", flush=True)
+            print(f"  score config G={eff[0]:2d} mode={eff[1]} carveout={eff[2]}: {ms / reps:.3f} ms", flush=True)
     best = min(table, key=table.get)
-    G, mode = (int(x) for x in best.split("/"))
-    glv.glv_set_score_config(index.dt, G, mode)
+    G, mode, carve = (int(x) for x in best.split("/"))
+    glv.glv_set_score_config(index.dt, G, mode, carve)
     if use_cache:
-        cache[key] = {"G": G, "mode": mode, "table": table}
+        cache[key] = {"G": G, "mode": mode, "carve": carve, "table": table}
         _save_cache(cache)
-    return G, mode, table
+    return G, mode, carve, table

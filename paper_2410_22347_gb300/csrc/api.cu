@@ -180,7 +180,7 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
                                         cand_ids, scores_scratch, d_status);
   if (st != GLV_OK || nq == 0) return st;
   GLV_CHECK(out_s && out_id, GLV_ERR_INVALID_ARG);
-  GLV_CHECK(fused_smem_bytes(C, d, dt) <= kSmemLimit - 12 * 1024, GLV_ERR_UNSUPPORTED);  // + static TopkSmem
+  GLV_CHECK(fused_smem_bytes(C, d, dt, kappa) <= kSmemLimit - 12 * 1024, GLV_ERR_UNSUPPORTED);  // + static TopkSmem
   GLV_LAUNCH(launch_score_topk(a, dt, nq, kappa, out_s, out_id, num_sms(), (cudaStream_t)stream));
   return GLV_OK;
 }
@@ -201,19 +201,23 @@ glv_status glv_score_lazy(const float* Q, int64_t nq, int32_t D, const float* A,
   return GLV_OK;
 }
 
-glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t gather_mode) {
+glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t gather_mode,
+                                int32_t smem_carveout_kb) {
   GLV_CHECK(valid_dt(dt), GLV_ERR_INVALID_ARG);
-  GLV_CHECK(set_score_config(dt, lanes_per_candidate, gather_mode), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(set_score_config(dt, lanes_per_candidate, gather_mode, smem_carveout_kb), GLV_ERR_INVALID_ARG);
   return GLV_OK;
 }
 
-glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate, int32_t* gather_mode) {
-  GLV_CHECK(valid_dt(dt) && d >= 1 && lanes_per_candidate && gather_mode, GLV_ERR_INVALID_ARG);
+glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate, int32_t* gather_mode,
+                                int32_t* smem_carveout_kb) {
+  GLV_CHECK(valid_dt(dt) && d >= 1 && lanes_per_candidate && gather_mode && smem_carveout_kb,
+            GLV_ERR_INVALID_ARG);
   const int nch = (int)(((int64_t)d * elem_bytes(dt) + 15) / 16);
-  int G = 0, mode = 0;
-  effective_score_config(dt, nch, &G, &mode);
+  int G = 0, mode = 0, carve = 0;
+  effective_score_config(dt, nch, &G, &mode, &carve);
   *lanes_per_candidate = G;
   *gather_mode = mode;
+  *smem_carveout_kb = carve;
   return GLV_OK;
 }
 
@@ -325,3 +329,14 @@ glv_status glv_kmeans_update(const float* X, int64_t N, int32_t D, const uint16_
 }
 
 }  // extern "C"
+
+glv_status glv_gather_rows(const void* rows, int64_t row_bytes, int64_t n_rows, const int32_t* ids, int64_t n_ids,
+                           float* out, int32_t* d_status, void* stream) {
+  GLV_CHECK(row_bytes >= 16 && row_bytes % 16 == 0 && n_rows >= 0 && n_ids >= 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(row_bytes <= 1024, GLV_ERR_UNSUPPORTED);
+  if (n_ids == 0) return GLV_OK;
+  GLV_CHECK(rows && ids && out && aligned(rows, 16), GLV_ERR_INVALID_ARG);
+  GLV_LAUNCH(launch_gather_rows(rows, row_bytes, n_rows, ids, n_ids, out, d_status, num_sms(),
+                                (cudaStream_t)stream));
+  return GLV_OK;
+}

@@ -55,9 +55,9 @@ struct RerankArgs {
 };
 
 cudaError_t launch_score(const ScoreArgs& a, int dt, int64_t nq, int num_sms, cudaStream_t st);
-size_t fused_smem_bytes(int C, int d, int dt);
-bool set_score_config(int dt, int G, int mode);
-void effective_score_config(int dt, int nch, int* G, int* mode);
+size_t fused_smem_bytes(int C, int d, int dt, int kappa);
+bool set_score_config(int dt, int G, int mode, int carve_kb);
+void effective_score_config(int dt, int nch, int* G, int* mode, int* carve_kb);
 cudaError_t launch_score_topk(const ScoreArgs& a, int dt, int64_t nq, int kappa, float* out_s,
                               int32_t* out_id, int num_sms, cudaStream_t st);
 size_t lazy_smem_bytes(int C, int d, int D, int dt);
@@ -66,6 +66,8 @@ cudaError_t launch_score_lazy(const ScoreArgs& a, int dt, int64_t nq, const floa
 cudaError_t launch_topk(const float* scores, const int64_t* off, const int32_t* ids, int64_t nq,
                         int kappa, float* out_s, int32_t* out_id, cudaStream_t st);
 cudaError_t launch_rerank(const RerankArgs& a, int64_t nq, bool vec, cudaStream_t st);
+cudaError_t launch_gather_rows(const void* rows, int64_t row_bytes, int64_t n_rows, const int32_t* ids,
+                               int64_t n_ids, float* out, int32_t* d_status, int num_sms, cudaStream_t st);
 size_t rerank_smem_bytes(int D, int kappa);
 cudaError_t launch_project_simt(const float* Q, int64_t nq, int D, const float* A, int64_t Mcols,
                                 float* Qp, cudaStream_t st);

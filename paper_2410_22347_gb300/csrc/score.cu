@@ -26,14 +26,15 @@ extern template cudaError_t launch_fused_dt<GLV_FP8_E4M3>(const ScoreArgs&, int6
 constexpr size_t kScoreSmemLimit = 227 * 1024 - 12 * 1024;  // leaves room for static shared memory
 
 static std::mutex g_cfg_mu;
-static ScoreConfig g_cfg[3] = {{0, 0}, {0, 0}, {0, 0}};  // G = 0: library default
+static ScoreConfig g_cfg[3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // G = 0: library default
 
-bool set_score_config(int dt, int G, int mode) {
+bool set_score_config(int dt, int G, int mode, int carve_kb) {
   if (dt < 0 || dt > 2 || mode < 0 || mode > 2) return false;
   const bool ok = (G == 0) || G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32;
   if (!ok) return false;
+  if (carve_kb != 0 && (carve_kb < 16 || carve_kb > 256)) return false;
   std::lock_guard<std::mutex> lk(g_cfg_mu);
-  g_cfg[dt] = {G, mode};
+  g_cfg[dt] = {G, mode, carve_kb};
   return true;
 }
 
@@ -52,17 +53,21 @@ static int qstride_of(int d, int dt) { return qp_qstride(nch_of(d, dt), dt); }
 
 ScoreConfig resolve_config(int dt, int nch) {
   const ScoreConfig t = get_score_config(dt);
+  ScoreConfig c;
   switch (dt) {
-    case GLV_F32: return effective_config<GLV_F32>(nch, t.G, t.mode);
-    case GLV_BF16: return effective_config<GLV_BF16>(nch, t.G, t.mode);
-    default: return effective_config<GLV_FP8_E4M3>(nch, t.G, t.mode);
+    case GLV_F32: c = effective_config<GLV_F32>(nch, t.G, t.mode); break;
+    case GLV_BF16: c = effective_config<GLV_BF16>(nch, t.G, t.mode); break;
+    default: c = effective_config<GLV_FP8_E4M3>(nch, t.G, t.mode); break;
   }
+  c.carve_kb = t.carve_kb;
+  return c;
 }
 
-void effective_score_config(int dt, int nch, int* G, int* mode) {
+void effective_score_config(int dt, int nch, int* G, int* mode, int* carve_kb) {
   const ScoreConfig c = resolve_config(dt, nch);
   *G = c.G;
   *mode = c.mode;
+  *carve_kb = c.carve_kb;
 }
 
 // Bulk gather needs its rings in shared memory; if they do not fit, use register loads.
@@ -95,9 +100,9 @@ cudaError_t launch_score(const ScoreArgs& a0, int dt, int64_t nq, int num_sms, c
   }
 }
 
-size_t fused_smem_bytes(int C, int d, int dt) {
+size_t fused_smem_bytes(int C, int d, int dt, int kappa) {
   const int eb = dt == GLV_F32 ? 4 : (dt == GLV_BF16 ? 2 : 1);
-  return score_smem(C, qstride_of(d, dt), true, 0, 0, (d * eb + 15) / 16, GLV_MAX_KAPPA).total();
+  return score_smem(C, qstride_of(d, dt), true, 0, 0, (d * eb + 15) / 16, kappa).total();
 }
 
 cudaError_t launch_score_topk(const ScoreArgs& a0, int dt, int64_t nq, int kappa, float* out_s,

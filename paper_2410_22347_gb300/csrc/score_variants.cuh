@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kScoreThreads) score_kernel(const ScoreArgs a,
 }
 
 // Gather-score and top-kappa of one query in one CTA: scores stay on chip as order-preserving
-// keys in shared memory and the radix selection runs there; a list longer than kFusedCache
+// keys in shared memory and the radix selection runs there; a list longer than the key cache
 // spills its scores to the caller's scratch (L2-resident during the selection passes).
 template <int DT, int G, int NCH, int MODE>
 __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH))
@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
     abort_flag = 0;
     S.sel_key = kc + kFusedCache;
     S.sel_id = reinterpret_cast<int32_t*>(kc + kFusedCache + kappa);
+    S.region = kc;
+    S.region_words = kFusedCache;
   }
   init_bulk_bars<MODE>(smem, L);
   const int64_t j = blockIdx.x;
@@ -146,20 +148,45 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
   const float* sj = scores + p0;
   const int32_t* ij = a.ids + p0;
   select_topk(
-      S, L_, kappa, [&](int64_t p) -> uint32_t { return cached ? kc[p] : score_key(sj[p]); },
+      S, L_, kappa, cached, [&](int64_t p) -> uint32_t { return cached ? kc[p] : score_key(sj[p]); },
       [&](int64_t p) -> int32_t { return ij[p]; }, out_s + j * kappa, out_id + j * kappa);
+}
+
+// Set kernel k's preferred shared-memory carveout: carve_kb > 0 caps it (when one CTA of
+// smem bytes fits under the cap), 0 restores the driver's choice.  The setting stays on the
+// function, so every launch sets it.
+inline cudaError_t apply_carveout(const void* k, size_t smem, int carve_kb) {
+  static int per_sm[64] = {0};
+  int pct = cudaSharedmemCarveoutDefault;
+  if (carve_kb > 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (per_sm[dev] == 0) {
+      e = cudaDeviceGetAttribute(&per_sm[dev], cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+      if (e != cudaSuccess) return e;
+    }
+    const int64_t cap = (int64_t)carve_kb * 1024;
+    if (per_sm[dev] > 0 && cap >= (int64_t)smem + 2048 && cap < per_sm[dev])
+      pct = (int)(cap * 100 / per_sm[dev]);
+  }
+  return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
 struct ScoreLaunch {
   const ScoreArgs& a;
   dim3 grid;
   int RB;
+  int carve_kb;
   cudaStream_t st;
   template <int DT, int G, int NCH, int MODE>
   cudaError_t go() {
     auto k = score_kernel<DT, G, NCH, MODE>;
     const size_t smem = score_smem(a.C, a.qstride, false, MODE, RB, a.nch).total();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = apply_carveout(reinterpret_cast<const void*>(k), smem, carve_kb);
     if (e != cudaSuccess) return e;
     k<<<grid, kScoreThreads, smem, st>>>(a, RB);
     return cudaGetLastError();
@@ -173,6 +200,7 @@ struct FusedLaunch {
   int kappa;
   float* out_s;
   int32_t* out_id;
+  int carve_kb;
   cudaStream_t st;
   template <int DT, int G, int NCH, int MODE>
   cudaError_t go() {
@@ -180,21 +208,22 @@ struct FusedLaunch {
     const size_t smem = score_smem(a.C, a.qstride, true, MODE, RB, a.nch, kappa).total();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = apply_carveout(reinterpret_cast<const void*>(k), smem, carve_kb);
+    if (e != cudaSuccess) return e;
     k<<<(unsigned)nq, kScoreThreads, smem, st>>>(a, RB, kappa, out_s, out_id);
     return cudaGetLastError();
-  }
-};
+  }};
 
 template <int DT>
 cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, int RB, ScoreConfig cfg, cudaStream_t st) {
-  ScoreLaunch f{a, grid, RB, st};
+  ScoreLaunch f{a, grid, RB, cfg.carve_kb, st};
   return dispatch_score<DT>(cfg.G, a.nch, cfg.mode, f);
 }
 
 template <int DT>
 cudaError_t launch_fused_dt(const ScoreArgs& a, int64_t nq, int RB, int kappa, float* out_s, int32_t* out_id,
                             ScoreConfig cfg, cudaStream_t st) {
-  FusedLaunch f{a, nq, RB, kappa, out_s, out_id, st};
+  FusedLaunch f{a, nq, RB, kappa, out_s, out_id, cfg.carve_kb, st};
   return dispatch_score<DT>(cfg.G, a.nch, cfg.mode, f);
 }
 

@@ -14,10 +14,12 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(const float* __restr
                                                            int kappa, float* __restrict__ out_s,
                                                            int32_t* __restrict__ out_id) {
   __shared__ TopkSmem S;
-  extern __shared__ uint32_t kcache[];  // kTopkCache keys, then kappa selected keys and ids
+  extern __shared__ __align__(16) uint32_t kcache[];  // kTopkCache keys, then kappa selected keys and ids
   if (threadIdx.x == 0) {
     S.sel_key = kcache + kTopkCache;
     S.sel_id = reinterpret_cast<int32_t*>(kcache + kTopkCache + kappa);
+    S.region = kcache;
+    S.region_words = kTopkCache;
   }
   const int64_t j = blockIdx.x;
   const int64_t p0 = off[j];
@@ -29,7 +31,7 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(const float* __restr
     for (int64_t p = threadIdx.x; p < L; p += blockDim.x) kcache[p] = score_key(sj[p]);
   __syncthreads();
   select_topk(
-      S, L, kappa, [&](int64_t p) -> uint32_t { return cached ? kcache[p] : score_key(sj[p]); },
+      S, L, kappa, cached, [&](int64_t p) -> uint32_t { return cached ? kcache[p] : score_key(sj[p]); },
       [&](int64_t p) -> int32_t { return ij[p]; }, out_s + j * kappa, out_id + j * kappa);
 }
 

@@ -5,10 +5,21 @@
 // Scores are mapped to order-preserving uint32 keys; a 4-pass radix select (8-bit digits,
 // most significant first) finds the kappa-th largest key K*.  Every key above K* is taken;
 // among keys equal to K* the smallest ids are taken, found by a second radix select on ~id
-// only when the tie group is larger than what is left.  The kappa winners are then placed by
-// rank ((key desc, id asc) ordering), which needs no sort network and is exact.  Histograms
-// use warp-aggregated shared-memory atomics (__match_any_sync), since similar scores pile
-// into one bucket.
+// only when the tie group is larger than what is left.  Histograms use warp-aggregated
+// shared-memory atomics (__match_any_sync), since similar scores pile into one bucket.
+//
+// Long lists that do not fit the CTA's key cache (kappa <= 256) are filtered first: the radix
+// select runs on a 256-key sample of the list to find a threshold T whose expected number of
+// list keys >= T is about 2 kappa, one pass copies the keys >= T (with their ids) into the then
+// unused key-cache region, and the selection runs there.  If fewer than kappa keys are >= T
+// (or the copy overflows), the selection runs on the whole list instead, so the result never
+// depends on the sample: when at least kappa keys are >= T, the kappa-th largest key is >= T
+// and every key that can be selected (ties included) is in the region.
+//
+// The kappa winners are sorted by (key desc, id asc).  After a filtered selection, up to 256
+// of them go through a bitonic network across the CTA's threads on the packed 64-bit value
+// key << 32 | ~id (exchanging through the key-cache region, free by then); otherwise each
+// entry counts the entries that rank before it.
 #pragma once
 
 #include "common.cuh"
@@ -18,14 +29,21 @@ namespace glv {
 constexpr int kTopkThreads = 256;
 constexpr int kTopkCache = 8192;
 
-// Radix histogram and counters; the kappa selected (key, id) pairs live in caller-provided
-// shared memory (kappa entries each), so the footprint follows kappa.
+// Radix histogram and counters.  The kappa selected (key, id) pairs live in caller-provided
+// shared memory (kappa entries each), so the footprint follows kappa; `region` (region_words
+// 32-bit words, at least 512, 8-byte aligned) is the caller's key cache, reused as scratch.
 struct TopkSmem {
   uint32_t hist[256];
-  uint32_t bucket, above, count, n_eq;
+  uint32_t bucket, above, count, n_eq, fill;
   uint32_t* sel_key;
   int32_t* sel_id;
+  uint32_t* region;
+  int region_words;
 };
+
+constexpr int kFilterMinList = 1024;  // shorter lists are selected directly
+constexpr int kFilterSample = 256;
+constexpr int kFilterMaxKappa = 256;
 
 // After the histogram is complete: find the digit b whose bucket holds the `want`-th
 // largest element (counting from the top), and how many elements lie in buckets above b.
@@ -94,12 +112,133 @@ GLV_DEV uint32_t radix_select(TopkSmem& S, int64_t L, uint32_t want, KeyOf key_o
   return prefix;
 }
 
+// Exact top-kappa of the keys key_of(p), p in [0, L), L > kappa, into S.sel_key / S.sel_id
+// (unordered, S.count entries).
+template <class KeyOf, class IdOf>
+GLV_DEV void select_unordered(TopkSmem& S, int64_t L, int kappa, KeyOf key_of, IdOf id_of) {
+  uint32_t need_eq = 0;
+  const uint32_t kstar = radix_select(S, L, (uint32_t)kappa, key_of, [](int64_t) { return true; }, &need_eq);
+  // everything strictly above K*: exactly kappa - need_eq entries
+  for (int64_t p = threadIdx.x; p < L; p += blockDim.x) {
+    const uint32_t k = key_of(p);
+    if (k > kstar) {
+      const uint32_t slot = atomicAdd(&S.count, 1u);
+      if (slot < (uint32_t)kappa) {
+        S.sel_key[slot] = k;
+        S.sel_id[slot] = id_of(p);
+      }
+    } else if (k == kstar) {
+      atomicAdd(&S.n_eq, 1u);
+    }
+  }
+  __syncthreads();
+  // the tie group at K*: all of it, or its need_eq smallest ids
+  uint32_t id_cut = 0;
+  const bool all_ties = (S.n_eq == need_eq);
+  if (!all_ties) {
+    uint32_t rem2 = 0;
+    id_cut = radix_select(S, L, need_eq, [&](int64_t p) { return ~(uint32_t)id_of(p); },
+                          [&](int64_t p) { return key_of(p) == kstar; }, &rem2);
+  }
+  for (int64_t p = threadIdx.x; p < L; p += blockDim.x) {
+    if (key_of(p) != kstar) continue;
+    const int32_t id = id_of(p);
+    if (all_ties || ~(uint32_t)id >= id_cut) {
+      const uint32_t slot = atomicAdd(&S.count, 1u);
+      if (slot < (uint32_t)kappa) {  // only repeated (id, score) pairs can overflow
+        S.sel_key[slot] = kstar;
+        S.sel_id[slot] = id;
+      }
+    }
+  }
+}
+
+// Threshold T from a sample of kFilterSample keys at evenly spread positions: the r-th largest
+// sample key, r chosen so that about 2 kappa + 32 list keys are expected to be >= T.  Returns
+// 0 (no filtering) when the list is too short for that to pay.
+template <class KeyOf>
+GLV_DEV uint32_t sample_threshold(TopkSmem& S, int64_t L, int kappa, KeyOf key_of) {
+  const int m = kFilterSample;
+  const int64_t want_hits = 2 * (int64_t)kappa + 32;
+  const int r = (int)((want_hits * m + L - 1) / L);
+  if (r < 1 || r > m / 2) return 0u;
+  uint32_t rem = 0;
+  return radix_select(S, m, (uint32_t)r, [&](int64_t t) { return key_of(t * L / m); },
+                      [](int64_t) { return true; }, &rem);
+}
+
+// Copy the keys >= T and their ids into the key-cache region (keys in the first half, ids in
+// the second); true if it holds between kappa and its capacity (S.fill entries), false if
+// the caller must select from the whole list.
+template <class KeyOf, class IdOf>
+GLV_DEV bool filter_to_region(TopkSmem& S, int64_t L, int kappa, uint32_t T, KeyOf key_of, IdOf id_of) {
+  const int cap = S.region_words / 2;
+  uint32_t* bk = S.region;
+  int32_t* bi = reinterpret_cast<int32_t*>(S.region + cap);
+  if (threadIdx.x == 0) S.fill = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = 0; b < L; b += blockDim.x) {
+    const int64_t p = b + threadIdx.x;
+    const uint32_t k = p < L ? key_of(p) : 0u;
+    const bool pass = p < L && k >= T;
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    if (bal == 0) continue;
+    uint32_t base = 0;
+    if (lane == __ffs(bal) - 1) base = atomicAdd(&S.fill, (uint32_t)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+    if (pass) {
+      const uint32_t slot = base + __popc(bal & ((1u << lane) - 1u));
+      if (slot < (uint32_t)cap) {
+        bk[slot] = k;
+        bi[slot] = id_of(p);
+      }
+    }
+  }
+  __syncthreads();
+  return S.fill >= (uint32_t)kappa && S.fill <= (uint32_t)cap;
+}
+
+// Sort the n (<= 256) selected pairs by (key desc, id asc) -- the packed value key << 32 | ~id
+// descending -- with a bitonic network over the first P = 2^ceil(log2 n) threads of the CTA,
+// one element per thread: partners closer than 32 are exchanged by warp shuffles, farther ones
+// through xs (256 slots of shared memory that are free at this point).  Writes out_s / out_id.
+GLV_DEV void block_sort_write(TopkSmem& S, int n, uint64_t* xs, float* out_s, int32_t* out_id) {
+  const int t = threadIdx.x;
+  int P = 2;
+  while (P < n) P <<= 1;
+  uint64_t v = t < n ? ((uint64_t)S.sel_key[t] << 32) | (uint32_t)(~(uint32_t)S.sel_id[t]) : 0ull;
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      uint64_t o = 0;
+      if (stride >= 32) {  // block-uniform branch: every thread reaches the barriers
+        if (t < P) xs[t] = v;
+        __syncthreads();
+        if (t < P) o = xs[t ^ stride];
+        __syncthreads();
+      } else if (t < ((P + 31) & ~31)) {  // whole warps that hold elements
+        o = __shfl_xor_sync(0xffffffffu, v, stride);
+      }
+      if (t < P) {
+        const bool take_max = ((t & stride) == 0) == ((t & size) == 0);
+        const uint64_t mx = v > o ? v : o, mn = v > o ? o : v;
+        v = take_max ? mx : mn;
+      }
+    }
+  }
+  if (t < n) {
+    out_s[t] = key_score((uint32_t)(v >> 32));
+    out_id[t] = (int32_t)(~(uint32_t)v);
+  }
+}
+
 // Select and write the sorted top kappa of L candidates: key_of(p) / id_of(p) give the key
-// and id of candidate p in [0, L).  Writes kappa (score, id) pairs to out_s / out_id, padded
+// and id of candidate p in [0, L); `in_region` says whether the keys are the ones cached in
+// S.region (else S.region is free).  Writes kappa (score, id) pairs to out_s / out_id, padded
 // with (-inf, -1).  All threads of the CTA must call it.
 template <class KeyOf, class IdOf>
-GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, KeyOf key_of, IdOf id_of, float* out_s,
-                         int32_t* out_id) {
+GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, bool in_region, KeyOf key_of, IdOf id_of,
+                         float* out_s, int32_t* out_id) {
   if (threadIdx.x == 0) {
     S.count = 0;
     S.n_eq = 0;
@@ -112,57 +251,41 @@ GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, KeyOf key_of, IdOf i
     }
     if (threadIdx.x == 0) S.count = (uint32_t)L;
   } else {
-    uint32_t need_eq = 0;
-    const uint32_t kstar =
-        radix_select(S, L, (uint32_t)kappa, key_of, [](int64_t) { return true; }, &need_eq);
-    // everything strictly above K*: exactly kappa - need_eq entries
-    for (int64_t p = threadIdx.x; p < L; p += blockDim.x) {
-      const uint32_t k = key_of(p);
-      if (k > kstar) {
-        const uint32_t slot = atomicAdd(&S.count, 1u);
-        if (slot < (uint32_t)kappa) {
-          S.sel_key[slot] = k;
-          S.sel_id[slot] = id_of(p);
-        }
-      } else if (k == kstar) {
-        atomicAdd(&S.n_eq, 1u);
-      }
-    }
-    __syncthreads();
-    // the tie group at K*: all of it, or its need_eq smallest ids
-    uint32_t id_cut = 0;
-    const bool all_ties = (S.n_eq == need_eq);
-    if (!all_ties) {
-      uint32_t rem2 = 0;
-      id_cut = radix_select(S, L, need_eq, [&](int64_t p) { return ~(uint32_t)id_of(p); },
-                            [&](int64_t p) { return key_of(p) == kstar; }, &rem2);
-    }
-    for (int64_t p = threadIdx.x; p < L; p += blockDim.x) {
-      if (key_of(p) != kstar) continue;
-      const int32_t id = id_of(p);
-      if (all_ties || ~(uint32_t)id >= id_cut) {
-        const uint32_t slot = atomicAdd(&S.count, 1u);
-        if (slot < (uint32_t)kappa) {  // only repeated (id, score) pairs can overflow
-          S.sel_key[slot] = kstar;
-          S.sel_id[slot] = id;
+    bool done = false;
+    if (kappa <= kFilterMaxKappa && L >= kFilterMinList) {
+      // lists cached on chip: the dense passes over shared memory are short, so they keep the
+      // plain path (the threshold's extra barriers cost more latency than they save)
+      const uint32_t T = in_region ? 0u : sample_threshold(S, L, kappa, key_of);
+      if (T != 0u) {
+        if (filter_to_region(S, L, kappa, T, key_of, id_of)) {
+          const uint32_t* bk = S.region;
+          const int32_t* bi = reinterpret_cast<const int32_t*>(S.region + S.region_words / 2);
+          select_unordered(S, (int64_t)S.fill, kappa, [bk](int64_t p) { return bk[p]; },
+                           [bi](int64_t p) { return bi[p]; });
+          done = true;
         }
       }
     }
+    if (!done) select_unordered(S, L, kappa, key_of, id_of);
   }
   __syncthreads();
   const int n = min((int)S.count, kappa);
-  // place by rank; identical entries are ordered by slot so every rank is written once
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const uint32_t ke = S.sel_key[e];
-    const int32_t ie = S.sel_id[e];
-    int rank = 0;
-    for (int f = 0; f < n; ++f) {
-      const uint32_t kf = S.sel_key[f];
-      const int32_t idf = S.sel_id[f];
-      rank += (ranks_before(kf, idf, ke, ie) || (kf == ke && idf == ie && f < e)) ? 1 : 0;
+  if (!in_region && n <= 256 && S.region_words >= 512 && blockDim.x >= 256) {
+    block_sort_write(S, n, reinterpret_cast<uint64_t*>(S.region), out_s, out_id);
+  } else {
+    // place by rank; identical entries are ordered by slot so every rank is written once
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const uint32_t ke = S.sel_key[e];
+      const int32_t ie = S.sel_id[e];
+      int rank = 0;
+      for (int f = 0; f < n; ++f) {
+        const uint32_t kf = S.sel_key[f];
+        const int32_t idf = S.sel_id[f];
+        rank += (ranks_before(kf, idf, ke, ie) || (kf == ke && idf == ie && f < e)) ? 1 : 0;
+      }
+      out_s[rank] = key_score(ke);
+      out_id[rank] = ie;
     }
-    out_s[rank] = key_score(ke);
-    out_id[rank] = ie;
   }
   for (int e = n + threadIdx.x; e < kappa; e += blockDim.x) {
     out_s[e] = -INFINITY;

@@ -51,9 +51,10 @@ def _load() -> ctypes.CDLL:
         "glv_score_topk": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, i32, P, P, P, P, P]),
         "glv_topk": (i32, [P, P, P, i64, i32, P, P, P]),
         "glv_score_lazy": (i32, [P, i64, i32, P, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P, P]),
-        "glv_set_score_config": (i32, [i32, i32, i32]),
-        "glv_get_score_config": (i32, [i32, i32, P, P]),
+        "glv_set_score_config": (i32, [i32, i32, i32, i32]),
+        "glv_get_score_config": (i32, [i32, i32, P, P, P]),
         "glv_rerank": (i32, [P, i64, i32, P, i64, P, i32, i32, P, P, P, P]),
+        "glv_gather_rows": (i32, [P, i64, i64, P, i64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -273,16 +274,24 @@ SCORE_GROUPS = {GLV_F32: (4, 8, 16, 32), GLV_BF16: (4, 8, 16, 32), GLV_FP8_E4M3:
 
 GATHER_MODES = (0, 1, 2)  # registers, registers pipelined, bulk copies into shared memory
 
+# shared-memory carveout caps the autotuner tries, KB (0 = the driver's choice; 164 leaves
+# about 92 KB of the SM's 256 KB to L1 for the rows in flight)
+SCORE_CARVEOUTS = (0, 164)
 
-def glv_set_score_config(dt: int, lanes_per_candidate: int, gather_mode: int) -> None:
-    _check("glv_set_score_config", _lib.glv_set_score_config(dt, int(lanes_per_candidate), int(gather_mode)))
+
+def glv_set_score_config(dt: int, lanes_per_candidate: int, gather_mode: int, smem_carveout_kb: int = 0) -> None:
+    _check("glv_set_score_config", _lib.glv_set_score_config(dt, int(lanes_per_candidate), int(gather_mode),
+                                                              int(smem_carveout_kb)))
 
 
-def glv_get_score_config(dt: int, d: int) -> tuple[int, int]:
+def glv_get_score_config(dt: int, d: int) -> tuple[int, int, int]:
+    """(lanes per candidate, gather mode, carveout cap KB) used for rows of width d."""
     g = ctypes.c_int32(0)
     p = ctypes.c_int32(0)
-    _check("glv_get_score_config", _lib.glv_get_score_config(dt, int(d), ctypes.byref(g), ctypes.byref(p)))
-    return int(g.value), int(p.value)
+    c = ctypes.c_int32(0)
+    _check("glv_get_score_config", _lib.glv_get_score_config(dt, int(d), ctypes.byref(g), ctypes.byref(p),
+                                                              ctypes.byref(c)))
+    return int(g.value), int(p.value), int(c.value)
 
 
 def glv_topk(scores, off, ids, kappa: int, out_s=None, out_id=None, stream=None):
@@ -312,3 +321,16 @@ def glv_rerank(X, Q, surv_id, k: int, out_s=None, out_id=None, d_status=None, st
     _check("glv_rerank", _lib.glv_rerank(_ptr(X), N, D, _ptr(Q), nq, _ptr(surv_id), kappa, k,
                                          _ptr(out_s), _ptr(out_id), _ptr(d_status), _stream(stream)))
     return out_s, out_id
+
+
+def glv_gather_rows(rows, row_bytes: int, ids, out=None, d_status=None, stream=None):
+    """Gather calibration: every row ids[p] of the row-major store ``rows`` (uint8, n_rows x
+    row_bytes) read whole, out[p] = its words summed as floats (no other arithmetic)."""
+    _need(rows, torch.uint8, "rows")
+    _need(ids, torch.int32, "ids", 1)
+    n_rows = rows.numel() // row_bytes
+    if out is None:
+        out = torch.empty(ids.shape[0], dtype=torch.float32, device=ids.device)
+    _check("glv_gather_rows", _lib.glv_gather_rows(_ptr(rows), int(row_bytes), n_rows, _ptr(ids), ids.shape[0],
+                                                   _ptr(out), _ptr(d_status), _stream(stream)))
+    return out

@@ -8,7 +8,9 @@ search of Algorithm 1 / Algorithm 4 with four library calls:
 
 ``search`` takes device tensors; ``search_host`` takes host tensors (pinned when given
 pinned memory), copies them in, searches and copies the top-k back on the same stream.
-Every step runs in libglv's kernels; torch only provides device memory and the stream.
+``HostSearchPipeline`` streams a sequence of host-resident batches: the copies of the next
+batch run on a copy stream while the current one is searched.  Every step runs in libglv's
+kernels; torch only provides device memory and the streams.
 """
 from __future__ import annotations
 
@@ -108,3 +110,69 @@ class GleanVecIndex:
 
     def reset_status(self):
         self.status.zero_()
+
+
+class HostSearchPipeline:
+    """Streams host-resident query batches through an index.
+
+    ``submit`` enqueues one batch (pinned host tensors: queries, CSR candidate lists, and the
+    top-k outputs) and returns at once.  The host-to-device copies of a batch run on a copy
+    stream, so they overlap the search of the batch before it on the compute stream; the
+    top-k of each batch is copied back on the compute stream right after its search.
+    Device input buffers rotate over ``depth`` slots: a slot is refilled only after the
+    search that read it has finished.  ``synchronize`` waits for everything submitted.
+    """
+
+    def __init__(self, index: GleanVecIndex, kappa: int, k: int, depth: int = 2, stream=None):
+        if depth < 2:
+            raise ValueError("depth >= 2 (one batch copying while another is searched)")
+        self.ix, self.kappa, self.k, self.depth = index, kappa, k, depth
+        self.compute = stream if stream is not None else torch.cuda.current_stream()
+        self.copy = torch.cuda.Stream(device=index.X.device)
+        self._slots = [None] * depth
+        self._done = [None] * depth
+        self._n = 0
+
+    def _slot(self, s: int, Q_h, off_h, ids_h):
+        key = (tuple(Q_h.shape), tuple(off_h.shape), tuple(ids_h.shape))
+        cur = self._slots[s]
+        if cur is None or cur[0] != key:
+            dev = self.ix.X.device
+            cur = (key, torch.empty(Q_h.shape, dtype=torch.float32, device=dev),
+                   torch.empty(off_h.shape, dtype=torch.int64, device=dev),
+                   torch.empty(ids_h.shape, dtype=torch.int32, device=dev))
+            self._slots[s] = cur
+        return cur[1:]
+
+    def begin(self):
+        """Order the copy stream after the work already enqueued on the compute stream (for
+        timing: an event recorded on the compute stream before begin() precedes every
+        copy submitted after it)."""
+        self.copy.wait_stream(self.compute)
+
+    def submit(self, Q_h: torch.Tensor, off_h: torch.Tensor, ids_h: torch.Tensor, out_s_h: torch.Tensor,
+               out_id_h: torch.Tensor) -> torch.cuda.Event:
+        s = self._n % self.depth
+        self._n += 1
+        Qd, offd, idsd = self._slot(s, Q_h, off_h, ids_h)
+        if self._done[s] is not None:
+            self.copy.wait_event(self._done[s])   # the search that last read this slot
+        with torch.cuda.stream(self.copy):
+            Qd.copy_(Q_h, non_blocking=True)
+            offd.copy_(off_h, non_blocking=True)
+            idsd.copy_(ids_h, non_blocking=True)
+            copied = torch.cuda.Event()
+            copied.record(self.copy)
+        self.compute.wait_event(copied)
+        with torch.cuda.stream(self.compute):
+            fs, fi = self.ix.search(Qd, offd, idsd, self.kappa, self.k, stream=self.compute)
+            out_s_h.copy_(fs, non_blocking=True)
+            out_id_h.copy_(fi, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(self.compute)
+        self._done[s] = done
+        return done
+
+    def synchronize(self):
+        self.compute.synchronize()
+        self.copy.synchronize()

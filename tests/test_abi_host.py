@@ -53,7 +53,7 @@ def _ret_i32(lib, name, argtypes):
 def test_host_validation_rejects_bad_arguments(lib):
     i64, i32 = ctypes.c_int64, ctypes.c_int32
     lib.glv_abi_version.restype = i32
-    assert lib.glv_abi_version() == 1
+    assert lib.glv_abi_version() == 2
     lib.glv_min_row_stride.restype = i64
     lib.glv_min_row_stride.argtypes = [i32, i32]
     assert lib.glv_min_row_stride(160, 0) == 640
@@ -119,6 +119,22 @@ def test_host_validation_rejects_bad_arguments(lib):
 
     lib.glv_status_string.restype = ctypes.c_char_p
     assert lib.glv_status_string(2) == b"id or tag out of range"
+
+    # scoring configuration: host-only state, checked without a GPU
+    setc = _ret_i32(lib, "glv_set_score_config", [i32, i32, i32, i32])
+    getc = _ret_i32(lib, "glv_get_score_config", [i32, i32, P, P, P])
+    g, m, c = i32(0), i32(0), i32(0)
+    ref = [ctypes.byref(x) for x in (g, m, c)]
+    assert setc(1, 4, 1, 164) == 0
+    assert getc(1, 160, *ref) == 0 and (g.value, m.value, c.value) == (4, 1, 164)
+    assert setc(1, 4, 1, 8) == INV          # carveout cap below 16 KB
+    assert setc(1, 4, 1, 300) == INV        # above the SM's shared memory
+    assert setc(1, 3, 0, 0) == INV          # lanes per candidate not a power of two
+    assert setc(1, 4, 3, 0) == INV          # no gather mode 3
+    assert setc(5, 4, 0, 0) == INV          # unknown store type
+    assert getc(1, 160, None, *ref[1:]) == INV
+    assert setc(1, 0, 0, 0) == 0
+    assert getc(1, 160, *ref) == 0 and c.value == 0
 
 
 def test_product_path_has_no_oracle_dependency():

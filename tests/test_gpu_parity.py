@@ -432,9 +432,11 @@ def test_search_pipeline_low_precision_recall(glv, dt_name):
 @pytest.mark.parametrize("nq,kappa", [(700, 100), (700, 1), (650, 1024), (40, 100)])
 def test_score_topk_fused_matches_separate(glv, dt_name, nq, kappa):
     dt = glv.DTYPES[dt_name]
-    rng, X, Q, mu, A, B, tags = _problem(nq + kappa, N=6000, D=96, d=40, C=7, nq=nq)
+    rng, X, Q, mu, A, B, tags = _problem(nq + kappa, N=17000, D=96, d=40, C=7, nq=nq)
     lens = rng.integers(0, 3000, nq)
-    lens[:5] = [0, 1, kappa, 2048, 2049]          # empty, single, exactly kappa, cache edge, spill
+    # empty, single, exactly kappa, the on-chip key-cache edge, and long lists whose scores
+    # spill to the scratch (the selection filters them through the sample threshold)
+    lens[:7] = [0, 1, kappa, 2048, 2049, 5000, 16500]
     lists = _ragged_lists(rng, nq, len(X), lens)
     lists[7] = np.concatenate([lists[7][:10], [len(X) + 5]])  # a bad id
     off, ids = _csr(lists)
@@ -488,6 +490,34 @@ def test_index_search_matches_oracle(glv):
     np.testing.assert_array_equal(hi.numpy(), fi)
 
 
+def test_host_pipeline_matches_search(glv):
+    """Batches streamed through HostSearchPipeline (copies of one batch overlapping the search
+    of the previous one, slots reused) give exactly the results of search() on each batch."""
+    from paper_2410_22347_gb300 import synth
+    from paper_2410_22347_gb300.index import GleanVecIndex, HostSearchPipeline
+    ws = [synth.make_workload(N=30000, D=128, d=32, C=9, nq=700, K_db=12, cands=900, kappa=40, k=10, cfg=87,
+                              replica=r) for r in range(5)]
+    X, A, B, mu = (_t(t.numpy()) for t in (ws[0].X, ws[0].A, ws[0].B, ws[0].mu))
+    ix = GleanVecIndex(X, A, B, mu=mu, store="bf16")
+    want = []
+    for w in ws:
+        fs, fi = ix.search(_t(w.Q.numpy()), _t(w.off.numpy()), _t(w.ids.numpy()), w.kappa, w.k)
+        want.append((fs.cpu().numpy().copy(), fi.cpu().numpy().copy()))
+    pipe = HostSearchPipeline(ix, ws[0].kappa, ws[0].k)
+    outs = []
+    for w in ws + ws[:2]:
+        o = (torch.empty(700, 10, dtype=torch.float32, pin_memory=True),
+             torch.empty(700, 10, dtype=torch.int32, pin_memory=True))
+        pipe.submit(w.Q.pin_memory(), w.off.pin_memory(), w.ids.pin_memory(), *o)
+        outs.append(o)
+    pipe.synchronize()
+    assert ix.device_status() == 0
+    for b, (s_h, i_h) in enumerate(outs):
+        ws_, wi = want[b % len(ws)]
+        np.testing.assert_array_equal(i_h.numpy(), wi)
+        np.testing.assert_array_equal(s_h.numpy().view(np.uint32), ws_.view(np.uint32))
+
+
 # ---------------------------------------------------------------------------------------
 # every scoring configuration the autotuner may pick stays exact
 # ---------------------------------------------------------------------------------------
@@ -524,18 +554,34 @@ def test_fused_matches_separate_in_every_gather_mode(glv, dt_name, mode, gi):
 def test_score_config_roundtrip(glv):
     try:
         glv.glv_set_score_config(glv.GLV_BF16, 8, 1)
-        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, 1)
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, 1, 0)
         # 8 lanes x 5 pipelined loads cannot cover a 160-chunk row: falls back to a default
-        g, m = glv.glv_get_score_config(glv.GLV_BF16, 1280)
+        g, m, _ = glv.glv_get_score_config(glv.GLV_BF16, 1280)
         assert m == 0
-        glv.glv_set_score_config(glv.GLV_BF16, 4, 2)
-        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (4, 2)
+        glv.glv_set_score_config(glv.GLV_BF16, 4, 2, 164)
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (4, 2, 164)
         with pytest.raises(glv.GlvError):
             glv.glv_set_score_config(glv.GLV_BF16, 3, 0)
         with pytest.raises(glv.GlvError):
             glv.glv_set_score_config(glv.GLV_BF16, 4, 3)
+        with pytest.raises(glv.GlvError):
+            glv.glv_set_score_config(glv.GLV_BF16, 4, 0, 8)
     finally:
         glv.glv_set_score_config(glv.GLV_BF16, 0, 0)
+
+
+@pytest.mark.parametrize("dt_name", ["bf16", "fp8"])
+def test_carveout_cap_changes_no_result(glv, dt_name):
+    """The carveout cap changes only the shared-memory / L1 split: scores and selections stay
+    bit-identical."""
+    dt = glv.DTYPES[dt_name]
+    try:
+        glv.glv_set_score_config(dt, 0, 0, 0)
+        test_score_topk_fused_matches_separate(glv, dt_name, 700, 100)
+        glv.glv_set_score_config(dt, 0, 0, 164)
+        test_score_topk_fused_matches_separate(glv, dt_name, 700, 100)
+    finally:
+        glv.glv_set_score_config(dt, 0, 0)
 
 
 # ---------------------------------------------------------------------------------------
@@ -572,3 +618,24 @@ def test_score_lazy_matches_oracle_and_counts_visited_clusters(glv, dt_name):
     scale = np.linalg.norm(Qp, axis=2)[cand_j, tags[ids]] * np.linalg.norm(xr_used, axis=1)[ids]
     ok, worst, bad = scores_close(got.cpu().numpy()[:len(ids)], ref, scale, TOL)
     assert ok, worst
+
+
+# ---------------------------------------------------------------------------------------
+# gather calibration kernel
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("row_bytes", [16, 48, 320, 1024])
+def test_gather_rows_sums_whole_rows(glv, row_bytes):
+    rng = _rng(row_bytes)
+    n_rows = 5000
+    vals = rng.integers(-8, 8, size=(n_rows, row_bytes // 4)).astype(np.float32)  # exact sums
+    rows = torch.from_numpy(vals.view(np.uint8).reshape(n_rows, row_bytes)).to("cuda:0")
+    ids = rng.integers(0, n_rows, size=20011).astype(np.int32)
+    ids[17] = n_rows + 3
+    ids[18] = -1
+    st = _status()
+    out = glv.glv_gather_rows(rows, row_bytes, _t(ids), d_status=st)
+    torch.cuda.synchronize()
+    assert st.item() == glv.GLV_ERR_BAD_ID
+    ref = np.where((ids >= 0) & (ids < n_rows), vals[np.clip(ids, 0, n_rows - 1)].sum(axis=1), 0.0)
+    np.testing.assert_array_equal(out.cpu().numpy(), ref.astype(np.float32))
