@@ -58,7 +58,7 @@ typedef enum {
  *                  the represented value is s_i * decode(code_ij). */
 typedef enum { GLV_F32 = 0, GLV_BF16 = 1, GLV_FP8_E4M3 = 2 } glv_dtype;
 
-#define GLV_ABI_VERSION 2
+#define GLV_ABI_VERSION 4
 #define GLV_MAX_KAPPA 1024 /* largest kappa accepted by glv_topk / glv_rerank */
 
 int32_t glv_abi_version(void);
@@ -209,18 +209,31 @@ glv_status glv_score_lazy(const float* Q, int64_t nq, int32_t D, const float* A,
 /* ---------------------------------------------------------------------------------------
  * Fused candidate scoring + top-kappa: the same computation and the same results (bit for
  * bit) as glv_score_candidates followed by glv_topk, without writing the scores to memory:
- * one CTA per query keeps them on chip and selects the kappa best there.
- *   Arguments as for glv_score_candidates and glv_topk.
- *   scores_scratch : cand_off[nq] float32 scratch.  Used for lists longer than 2048
- *                    candidates and when nq is small (the lists are then split over many
- *                    CTAs and the selection runs afterwards); otherwise left untouched.
+ * they stay on chip and the kappa best are selected there.  Work is planned on the device:
+ * a query's list is one work item, or -- when it holds at least 8192 candidates --
+ * floor(L / 4096) items (the last one takes the remainder), each selecting its own
+ * top-kappa, merged by the item that finishes last (the merged top-kappa is exact);
+ * persistent CTAs claim items dynamically, so long lists do not leave a tail of busy CTAs.
+ *   Arguments as for glv_score_candidates and glv_topk, and:
+ *   n_candidates   : cand_off[nq] - cand_off[0], the number of candidate entries (the
+ *                    length of cand_ids).  If the lists hold more, nothing is computed and
+ *                    GLV_ERR_INVALID_ARG is reported in d_status.
+ *   scores_scratch : n_candidates float32 scratch (per-item top-kappa lists of split
+ *                    queries, scores of lists that exceed the on-chip key cache, and the
+ *                    scores when nq is small -- the lists are then split over many CTAs and
+ *                    the selection runs afterwards); contents on entry do not matter.
+ *   workspace      : glv_score_topk_workspace_size(nq, n_candidates) bytes, 256-byte
+ *                    aligned (the work plan); contents on entry do not matter.
  *   out_s, out_id  : nq x kappa outputs, as glv_topk.
+ * Calls on the same workspace must not overlap in time.
  * ------------------------------------------------------------------------------------- */
+size_t glv_score_topk_workspace_size(int64_t nq, int64_t n_candidates);
 glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, const void* Xred,
                           int64_t row_stride, const float* scales, glv_dtype dt,
                           const uint16_t* tags, int64_t N, const int64_t* cand_off,
-                          const int32_t* cand_ids, int32_t kappa, float* scores_scratch,
-                          float* out_s, int32_t* out_id, int32_t* d_status, void* stream);
+                          const int32_t* cand_ids, int64_t n_candidates, int32_t kappa,
+                          float* scores_scratch, void* workspace, float* out_s, int32_t* out_id,
+                          int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Scoring configuration (the autotuner's hook; no counterpart in the paper).  Per store
@@ -235,15 +248,19 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
  * memory part of the SM's shared-memory / L1 split for the scoring kernels (0 = the
  * driver's choice, else 16..256 KB; ignored where one CTA would not fit under the cap): the
  * driver sizes that split for the kernel's full occupancy, and the L1 left over stages the
- * gathered rows in flight, so fewer CTAs with more L1 can be faster.  It changes only speed.
- * A choice that cannot serve a row width falls back to the default for that width;
- * glv_get_score_config reports the configuration used for rows of width d.  Process-wide
- * setting.  Errors: GLV_ERR_INVALID_ARG for an unknown dt, lane count, mode or carveout.
+ * gathered rows in flight, so fewer CTAs with more L1 can be faster.  schedule (fused call
+ * only): 1 (default) = the planned work items of glv_score_topk (long lists cut into chunks,
+ * persistent CTAs); 0 = one CTA per query, no plan (faster when no list is long: no plan
+ * launch, no work counter).  All of these change only speed.  The fused call maps gather
+ * mode 2 to mode 0.  A choice that cannot serve a row width falls back to the default for
+ * that width; glv_get_score_config reports the configuration used for rows of width d.
+ * Process-wide setting.  Errors: GLV_ERR_INVALID_ARG for an unknown dt, lane count, mode,
+ * carveout or schedule.
  * ------------------------------------------------------------------------------------- */
 glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t gather_mode,
-                                int32_t smem_carveout_kb);
+                                int32_t smem_carveout_kb, int32_t schedule);
 glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate,
-                                int32_t* gather_mode, int32_t* smem_carveout_kb);
+                                int32_t* gather_mode, int32_t* smem_carveout_kb, int32_t* schedule);
 
 /* ---------------------------------------------------------------------------------------
  * Gather calibration (no counterpart in the paper; a measuring instrument for the roofline

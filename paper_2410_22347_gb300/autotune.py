@@ -24,7 +24,7 @@ CACHE = os.environ.get("GLV_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"
 
 def _key(dt: int, d: int, C: int, mean_len: float) -> str:
     name = torch.cuda.get_device_name()
-    return f"v2|{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
+    return f"v3|{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
 
 
 def _load_cache() -> dict:
@@ -47,31 +47,34 @@ def _save_cache(c: dict) -> None:
 
 
 def configurations(dt: int):
+    # the fused call gathers into registers (modes 0 and 1; it maps the bulk mode to 0)
     for G in glv.SCORE_GROUPS[dt]:
-        for mode in glv.GATHER_MODES:
+        for mode in (0, 1):
             for carve in glv.SCORE_CARVEOUTS:
-                yield G, mode, carve
+                for sched in glv.SCORE_SCHEDULES:
+                    yield G, mode, carve, sched
 
 
 def tune_score(index, Q, off, ids, kappa: int, reps: int = 5, use_cache: bool = True, verbose: bool = False):
     """Pick the fastest scoring configuration for ``index``'s store on this workload.
-    Returns (G, gather_mode, carveout_kb, table) where table maps "G/mode/carveout" to the
-    mean ms per call."""
+    Returns (G, gather_mode, carveout_kb, schedule, table) where table maps
+    "G/mode/carveout/schedule" to the mean ms per call."""
     nq = Q.shape[0]
     mean_len = ids.shape[0] / max(nq, 1)
     key = _key(index.dt, index.d, index.C, mean_len) + f"|k{kappa}"
     cache = _load_cache() if use_cache else {}
     if key in cache:
-        G, mode, carve = cache[key]["G"], cache[key]["mode"], cache[key].get("carve", 0)
-        glv.glv_set_score_config(index.dt, G, mode, carve)
-        return G, mode, carve, cache[key].get("table", {})
+        e = cache[key]
+        G, mode, carve, sched = e["G"], e["mode"], e.get("carve", 0), e.get("sched", 1)
+        glv.glv_set_score_config(index.dt, G, mode, carve, sched)
+        return G, mode, carve, sched, e.get("table", {})
     b = index._buffers(nq, ids.shape[0], kappa, kappa)
     glv.glv_project_queries(Q, index.A, index.compute, Qp=b["Qp"], workspace=b["pws"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=Q.device)  # 256 MB > L2
     table = {}
     seen = set()
-    for G, mode, carve in configurations(index.dt):
-        glv.glv_set_score_config(index.dt, G, mode, carve)
+    for G, mode, carve, sched in configurations(index.dt):
+        glv.glv_set_score_config(index.dt, G, mode, carve, sched)
         eff = glv.glv_get_score_config(index.dt, index.d)
         if eff in seen:  # this choice cannot serve the row width; it maps onto one already timed
             continue
@@ -79,7 +82,7 @@ def tune_score(index, Q, off, ids, kappa: int, reps: int = 5, use_cache: bool = 
 
         def run():
             glv.glv_score_topk(b["Qp"], index.Xred, index.row_stride, index.scales, index.dt, index.tags, off,
-                               ids, kappa, scores_scratch=b["scores"], out_s=b["ts"], out_id=b["ti"])
+                               ids, kappa, scores_scratch=b["scores"], workspace=b["tws"], out_s=b["ts"], out_id=b["ti"])
         run()
         torch.cuda.synchronize()
         ms = 0.0
@@ -91,13 +94,14 @@ def tune_score(index, Q, off, ids, kappa: int, reps: int = 5, use_cache: bool = 
             e1.record()
             e1.synchronize()
             ms += e0.elapsed_time(e1)
-        table[f"{eff[0]}/{eff[1]}/{eff[2]}"] = ms / reps
+        table["/".join(str(x) for x in eff)] = ms / reps
         if verbose:
-            print(f"  score config G={eff[0]:2d} mode={eff[1]} carveout={eff[2]}: {ms / reps:.3f} ms", flush=True)
+            print(f"  score config G={eff[0]:2d} mode={eff[1]} carveout={eff[2]} schedule={eff[3]}: "
+                  f"{ms / reps:.3f} ms", flush=True)
     best = min(table, key=table.get)
-    G, mode, carve = (int(x) for x in best.split("/"))
-    glv.glv_set_score_config(index.dt, G, mode, carve)
+    G, mode, carve, sched = (int(x) for x in best.split("/"))
+    glv.glv_set_score_config(index.dt, G, mode, carve, sched)
     if use_cache:
-        cache[key] = {"G": G, "mode": mode, "carve": carve, "table": table}
+        cache[key] = {"G": G, "mode": mode, "carve": carve, "sched": sched, "table": table}
         _save_cache(cache)
-    return G, mode, carve, table
+    return G, mode, carve, sched, table

@@ -169,19 +169,26 @@ glv_status glv_score_candidates(const float* Qp, int64_t nq, int32_t C, int32_t 
   return GLV_OK;
 }
 
+size_t glv_score_topk_workspace_size(int64_t nq, int64_t n_candidates) {
+  if (nq < 0 || n_candidates < 0) return 0;
+  return topk_plan_bytes(nq, n_candidates);
+}
+
 glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, const void* Xred,
                           int64_t row_stride, const float* scales, glv_dtype dt,
                           const uint16_t* tags, int64_t N, const int64_t* cand_off,
-                          const int32_t* cand_ids, int32_t kappa, float* scores_scratch,
-                          float* out_s, int32_t* out_id, int32_t* d_status, void* stream) {
-  GLV_CHECK(kappa >= 1 && kappa <= GLV_MAX_KAPPA, GLV_ERR_INVALID_ARG);
+                          const int32_t* cand_ids, int64_t n_candidates, int32_t kappa, float* scores_scratch,
+                          void* workspace, float* out_s, int32_t* out_id, int32_t* d_status, void* stream) {
+  GLV_CHECK(kappa >= 1 && kappa <= GLV_MAX_KAPPA && n_candidates >= 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(nq + n_candidates / kChunk + 1 <= 2147483647LL, GLV_ERR_UNSUPPORTED);
   ScoreArgs a;
   const glv_status st = fill_score_args(a, Qp, nq, C, d, Xred, row_stride, scales, dt, tags, N, cand_off,
                                         cand_ids, scores_scratch, d_status);
   if (st != GLV_OK || nq == 0) return st;
-  GLV_CHECK(out_s && out_id, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(out_s && out_id && workspace && aligned(workspace, 256), GLV_ERR_INVALID_ARG);
   GLV_CHECK(fused_smem_bytes(C, d, dt, kappa) <= kSmemLimit - 12 * 1024, GLV_ERR_UNSUPPORTED);  // + static TopkSmem
-  GLV_LAUNCH(launch_score_topk(a, dt, nq, kappa, out_s, out_id, num_sms(), (cudaStream_t)stream));
+  GLV_LAUNCH(launch_score_topk(a, dt, nq, n_candidates, kappa, workspace, out_s, out_id, num_sms(),
+                               (cudaStream_t)stream));
   return GLV_OK;
 }
 
@@ -202,22 +209,23 @@ glv_status glv_score_lazy(const float* Q, int64_t nq, int32_t D, const float* A,
 }
 
 glv_status glv_set_score_config(glv_dtype dt, int32_t lanes_per_candidate, int32_t gather_mode,
-                                int32_t smem_carveout_kb) {
+                                int32_t smem_carveout_kb, int32_t schedule) {
   GLV_CHECK(valid_dt(dt), GLV_ERR_INVALID_ARG);
-  GLV_CHECK(set_score_config(dt, lanes_per_candidate, gather_mode, smem_carveout_kb), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(set_score_config(dt, lanes_per_candidate, gather_mode, smem_carveout_kb, schedule), GLV_ERR_INVALID_ARG);
   return GLV_OK;
 }
 
 glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_candidate, int32_t* gather_mode,
-                                int32_t* smem_carveout_kb) {
-  GLV_CHECK(valid_dt(dt) && d >= 1 && lanes_per_candidate && gather_mode && smem_carveout_kb,
+                                int32_t* smem_carveout_kb, int32_t* schedule) {
+  GLV_CHECK(valid_dt(dt) && d >= 1 && lanes_per_candidate && gather_mode && smem_carveout_kb && schedule,
             GLV_ERR_INVALID_ARG);
   const int nch = (int)(((int64_t)d * elem_bytes(dt) + 15) / 16);
-  int G = 0, mode = 0, carve = 0;
-  effective_score_config(dt, nch, &G, &mode, &carve);
+  int G = 0, mode = 0, carve = 0, sched = 1;
+  effective_score_config(dt, nch, &G, &mode, &carve, &sched);
   *lanes_per_candidate = G;
   *gather_mode = mode;
   *smem_carveout_kb = carve;
+  *schedule = sched;
   return GLV_OK;
 }
 

@@ -55,6 +55,18 @@ GLV_DEV float key_score(uint32_t k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
+// 8-byte asynchronous copy global -> shared (cp.async; completes at cp_async_wait_all).
+GLV_DEV void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+GLV_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Ids as unsigned keys that grow as the (signed) id shrinks: ties between equal scores go to
+// the smaller id, negative (invalid) ids included, in every selection path.
+GLV_DEV uint32_t id_rank(int32_t id) { return ~((uint32_t)id ^ 0x80000000u); }
+GLV_DEV int32_t id_from_rank(uint32_t r) { return (int32_t)(~r ^ 0x80000000u); }
+
 // (score, id) ordering: a ranks before b.
 GLV_DEV bool ranks_before(uint32_t ka, int32_t ia, uint32_t kb, int32_t ib) {
   return ka > kb || (ka == kb && ia < ib);

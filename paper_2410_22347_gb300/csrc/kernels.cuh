@@ -56,10 +56,35 @@ struct RerankArgs {
 
 cudaError_t launch_score(const ScoreArgs& a, int dt, int64_t nq, int num_sms, cudaStream_t st);
 size_t fused_smem_bytes(int C, int d, int dt, int kappa);
-bool set_score_config(int dt, int G, int mode, int carve_kb);
-void effective_score_config(int dt, int nch, int* G, int* mode, int* carve_kb);
-cudaError_t launch_score_topk(const ScoreArgs& a, int dt, int64_t nq, int kappa, float* out_s,
-                              int32_t* out_id, int num_sms, cudaStream_t st);
+
+// Work plan of the fused scoring + top-kappa, built on the device (plan_chunks): a query's
+// list is one work item, or -- when it holds at least 2 kChunk candidates -- floor(L / kChunk)
+// items of kChunk candidates, the last one taking the remainder (so every item has at least
+// kChunk >= 2 kappa candidates and can hold its own top-kappa list in its part of the score
+// scratch); the item that finishes last merges the items' lists.
+constexpr int kChunk = 4096;
+struct ItemRec {
+  int64_t b0;       // first candidate of the item (a position in cand_ids)
+  int32_t len;      // candidates in the item
+  int32_t q;        // query
+  int32_t c;        // chunk index within the query
+  int32_t nchunks;  // items of the query
+};
+struct ChunkPlan {
+  int32_t* next;         // next work item to claim (dynamic scheduling)
+  int32_t* n_items;      // number of work items
+  int32_t* chunk_start;  // nq + 1: first item of each query
+  int32_t* done;         // nq: finished items per query
+  ItemRec* items;        // the work items, query-major
+};
+size_t topk_plan_bytes(int64_t nq, int64_t n_cand);
+ChunkPlan topk_plan_layout(void* ws, int64_t nq);
+cudaError_t launch_plan_chunks(const int64_t* off, int64_t nq, int64_t n_cand, void* ws, int32_t* d_status,
+                               cudaStream_t st);
+bool set_score_config(int dt, int G, int mode, int carve_kb, int sched);
+void effective_score_config(int dt, int nch, int* G, int* mode, int* carve_kb, int* sched);
+cudaError_t launch_score_topk(const ScoreArgs& a, int dt, int64_t nq, int64_t n_cand, int kappa, void* plan_ws,
+                              float* out_s, int32_t* out_id, int num_sms, cudaStream_t st);
 size_t lazy_smem_bytes(int C, int d, int D, int dt);
 cudaError_t launch_score_lazy(const ScoreArgs& a, int dt, int64_t nq, const float* Q, int D, const float* A,
                               int32_t* visited, cudaStream_t st);

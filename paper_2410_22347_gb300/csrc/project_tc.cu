@@ -16,7 +16,8 @@
 //   warp 1      TMEM owner + MMA issuer (one lane): 128 x 256 FP32 accumulator, double
 //               buffered in TMEM (2 x 256 columns) so the epilogue of tile t overlaps the
 //               MMAs of tile t+1;
-//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 32 columns at a time -> FP32 global stores.
+//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 32 columns at a time, transposed through a
+//               padded shared-memory tile -> coalesced FP32 global stores (128 B per row).
 // Every mbarrier wait is bounded (see tc.cuh); a timeout sets GLV_ERR_TIMEOUT in d_status,
 // all roles leave their loops, outstanding TMA loads and MMAs are drained (bounded), and the
 // TMEM is freed before the CTA exits.
@@ -49,7 +50,9 @@ struct TcCfg {
   static constexpr int kKPerStage = kTcRowBytes / kElemBytes;
   static constexpr int kKPerMma = MODE == 0 ? 16 : 8;     // 32 bytes of K per MMA
   static constexpr int kMmaPerStage = kKPerStage / kKPerMma;
-  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 + 256;
+  // epilogue staging: per epilogue warp a 32 x 32 FP32 tile, rows padded to 33 words
+  static constexpr size_t kEpiBytes = 4 * 32 * 33 * sizeof(float);
+  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 + 256 + kEpiBytes;
 };
 
 struct TcArgs {
@@ -60,7 +63,6 @@ struct TcArgs {
   int tiles_n;
   int64_t num_tiles;
   int32_t* d_status;
-  int vec;          // N % 4 == 0 and out 16-byte aligned: float4 stores
 };
 
 template <int MODE>
@@ -78,6 +80,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* epi = reinterpret_cast<float*>(smem + (size_t)Cfg::kStages * Cfg::kStageBytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -215,28 +218,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       (void)tc::mbar_try_wait(&tfull[acc], acc_phase);
       tc::tc_fence_after();
       const int tm = (int)(t / args.tiles_n), tn = (int)(t % args.tiles_n);
-      const int64_t row = (int64_t)tm * kTcBM + q * 32 + lane;
-      float* orow = args.out + row * args.N;
-      const bool vec = args.vec != 0;
+      const int64_t row_base = (int64_t)tm * kTcBM + q * 32;
+      // lane = row in TMEM; each 32 x 32 chunk goes through the warp's shared-memory tile
+      // (conflict-free: rows padded to 33 words) so the global stores write one row segment
+      // of 32 consecutive columns (128 bytes) per instruction
+      float* stg = epi + (warp - 2) * (32 * 33);
 #pragma unroll 1
       for (int ch = 0; ch < kTcBN / 32; ++ch) {
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kTcBN + ch * 32), r);
         tc::tmem_ld_wait();
-        const int64_t col0 = (int64_t)tn * kTcBN + ch * 32;
-        if (row < args.M) {
-          if (vec && col0 + 32 <= args.N) {
-            float4* o4 = reinterpret_cast<float4*>(orow + col0);
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-              o4[u] = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
-                                  __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
-          } else {
-#pragma unroll
-            for (int u = 0; u < 32; ++u)
-              if (col0 + u < args.N) orow[col0 + u] = __uint_as_float(r[u]);
+        for (int u = 0; u < 32; ++u) stg[lane * 33 + u] = __uint_as_float(r[u]);
+        __syncwarp();
+        const int64_t col = (int64_t)tn * kTcBN + ch * 32 + lane;
+        if (col < args.N) {
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t row = row_base + rr;
+            if (row < args.M) args.out[row * args.N + col] = stg[rr * 33 + lane];
           }
         }
+        __syncwarp();
       }
       tc::tc_fence_before();
       tc::mbar_arrive(&tempty[acc]);
@@ -405,7 +408,6 @@ cudaError_t launch_project_tc(const float* Q, int64_t nq, int D, const float* A,
   args.tiles_n = (int)((Mc + kTcBN - 1) / kTcBN);
   args.num_tiles = ((nq + kTcBM - 1) / kTcBM) * (int64_t)args.tiles_n;
   args.d_status = d_status;
-  args.vec = (Mc % 4 == 0) && ((uintptr_t)Qp % 16 == 0);
   const int grid = (int)(args.num_tiles < num_sms ? args.num_tiles : num_sms);
   if (bf16) {
     auto k = project_tc_kernel<0>;

@@ -73,14 +73,15 @@ cudaError_t dispatch_score(int G, int nch, int mode, F& f) {
 
 // Effective configuration for a row of nch chunks: the tuned choice if it can serve the
 // row, else the default group (or 32 lanes for wide rows) with register loads.
-// Lanes per candidate, gather mode, and the shared-memory carveout cap in KB (0 = the
-// driver's choice).  The driver sizes the shared-memory / L1 split for the kernel's full
+// Lanes per candidate, gather mode, the shared-memory carveout cap in KB (0 = the driver's
+// choice) and the fused call's schedule.  The driver sizes the shared-memory / L1 split for the kernel's full
 // occupancy, and the L1 that is left stages the rows in flight, so a smaller carveout (fewer
 // CTAs, more L1) can gather faster; which one wins depends on the store, d and C.
 struct ScoreConfig {
   int G;
   int mode;
   int carve_kb = 0;
+  int sched = 1;  // fused call: 1 = planned work items (chunked long lists), 0 = one CTA per query
 };
 
 template <int DT>

@@ -110,46 +110,130 @@ __global__ void __launch_bounds__(kScoreThreads) score_kernel(const ScoreArgs a,
   }
 }
 
-// Gather-score and top-kappa of one query in one CTA: scores stay on chip as order-preserving
-// keys in shared memory and the radix selection runs there; a list longer than the key cache
-// spills its scores to the caller's scratch (L2-resident during the selection passes).
+// Gather-score and top-kappa, persistent: each CTA claims work items (a whole candidate list,
+// or a chunk of at most kChunk candidates of a long one) from the plan until none is left.
+// Scores stay on chip as order-preserving keys in shared memory and the radix selection runs
+// there; an item longer than the key cache spills its scores to the caller's scratch.  A chunk
+// of a long list writes its own top-kappa at the start of its part of the scratch (scores then
+// ids); the CTA that finishes a query's last chunk (a fenced per-query counter; nothing waits)
+// selects the query's top-kappa from the chunks' lists, which contain it: a candidate outside
+// its chunk's top-kappa has kappa candidates of that chunk ranked before it.
 template <int DT, int G, int NCH, int MODE>
 __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH))
-    score_topk_kernel(const ScoreArgs a, int RB, int kappa, float* out_s, int32_t* out_id) {
+    score_topk_kernel(const ScoreArgs a, int kappa, ChunkPlan plan, int direct, float* out_s, int32_t* out_id) {
+  static_assert(MODE != 2, "the fused kernel gathers rows into registers");
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ TopkSmem S;
-  __shared__ int abort_flag;
-  const ScoreSmem L = score_smem(a.C, a.qstride, true, MODE, RB, a.nch, kappa);
+  // work items, double-buffered: slot cur holds the current item, thread 0 fills the other
+  // slot with the next one while the current one is being selected
+  __shared__ __align__(16) ItemRec s_rec[2];
+  __shared__ int s_valid[2], s_last, s_claimed, s_items;  // s_claimed: next item, claimed ahead
+  __shared__ int64_t s_staged;
+  const ScoreSmem L = score_smem(a.C, a.qstride, true, MODE, 0, a.nch, kappa);
+  float* qs = reinterpret_cast<float*>(smem);
   uint32_t* kc = reinterpret_cast<uint32_t*>(smem + L.qs_bytes);
   if (threadIdx.x == 0) {
-    abort_flag = 0;
     S.sel_key = kc + kFusedCache;
     S.sel_id = reinterpret_cast<int32_t*>(kc + kFusedCache + kappa);
     S.region = kc;
     S.region_words = kFusedCache;
+    s_staged = -1;
+    if (direct) {  // one CTA per query, no plan: the query's whole list is the only item
+      const int64_t q = blockIdx.x, p0 = a.off[q];
+      s_rec[0].b0 = p0;
+      s_rec[0].len = (int32_t)(a.off[q + 1] - p0);
+      s_rec[0].q = (int32_t)q;
+      s_rec[0].c = 0;
+      s_rec[0].nchunks = 1;
+      s_valid[0] = 1;
+      s_items = 0;
+      s_claimed = 0;
+    } else {
+      s_items = *plan.n_items;
+      const int first = atomicAdd(plan.next, 1);
+      s_valid[0] = first < s_items;
+      if (s_valid[0]) s_rec[0] = plan.items[first];
+      s_claimed = atomicAdd(plan.next, 1);
+    }
   }
-  init_bulk_bars<MODE>(smem, L);
-  const int64_t j = blockIdx.x;
-  stage_qp<DT>(a, j, reinterpret_cast<float*>(smem));
   __syncthreads();
-  const int64_t p0 = a.off[j], p1 = a.off[j + 1];
-  const int64_t L_ = p1 - p0;
-  const bool cached = L_ <= kFusedCache;
   float* scores = a.scores;
-  if (cached) {
-    auto sink = [kc, p0](int64_t p, float s) { kc[p - p0] = score_key(s); };
-    score_span<DT, G, NCH, MODE>(a, smem, L, RB, p0, p1, sink, &abort_flag);
-  } else {
-    auto sink = [scores](int64_t p, float s) { scores[p] = s; };
-    score_span<DT, G, NCH, MODE>(a, smem, L, RB, p0, p1, sink, &abort_flag);
+  for (int cur = 0;; cur ^= 1) {
+    if (!s_valid[cur]) break;
+    const int64_t j = s_rec[cur].q;
+    if (j != s_staged) stage_qp<DT>(a, j, qs);
+    __syncthreads();
+    if (threadIdx.x == 0) s_staged = j;
+    const int64_t b0 = s_rec[cur].b0, b1 = b0 + s_rec[cur].len;
+    if (b1 - b0 <= kFusedCache) {
+      auto sink = [kc, b0](int64_t p, float s) { kc[p - b0] = score_key(s); };
+      score_range<DT, G, NCH, MODE == 1>(a, qs, b0, b1, sink);
+    } else {
+      auto sink = [scores](int64_t p, float s) { scores[p] = s; };
+      score_range<DT, G, NCH, MODE == 1>(a, qs, b0, b1, sink);
+    }
+    // thread 0: copy the next item's record into the other slot asynchronously and claim the
+    // item after it; both land while the current item is being selected (nothing here waits)
+    int claim_ahead = 0;
+    if (threadIdx.x == 0) {
+      const int claimed = s_claimed;
+      const bool has_nxt = claimed < s_items;
+      s_valid[cur ^ 1] = has_nxt;
+      if (has_nxt) {
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(plan.items + claimed);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&s_rec[cur ^ 1]);
+#pragma unroll
+        for (int w = 0; w < (int)(sizeof(ItemRec) / 8); ++w) cp_async8(dst + w, src + w);
+        claim_ahead = atomicAdd(plan.next, 1);
+      } else {
+        claim_ahead = claimed;
+      }
+    }
+    __syncthreads();
+    // re-read the item after the barrier (nothing of it stays live across the gather)
+    const int nchunks = s_rec[cur].nchunks;
+    const int64_t jj = s_rec[cur].q, c0 = s_rec[cur].b0, lc = s_rec[cur].len;
+    const bool in_kc = lc <= kFusedCache;
+    const float* sj = scores + c0;
+    const int32_t* ij = a.ids + c0;
+    if (nchunks == 1) {
+      select_topk(
+          S, lc, kappa, in_kc, [&](int64_t p) -> uint32_t { return in_kc ? kc[p] : score_key(sj[p]); },
+          [&](int64_t p) -> int32_t { return ij[p]; }, out_s + jj * kappa, out_id + jj * kappa);
+    } else {
+      // the chunk's unordered top-kappa goes to the start of its own part of the scratch
+      // (scores, then ids): every chunk has at least kChunk >= 2 kappa candidates, and its
+      // spilled scores have all been read when the list is written
+      float* ps = scores + c0;
+      select_topk(
+          S, lc, kappa, in_kc, [&](int64_t p) -> uint32_t { return in_kc ? kc[p] : score_key(sj[p]); },
+          [&](int64_t p) -> int32_t { return ij[p]; }, ps, reinterpret_cast<int32_t*>(ps + kappa), false);
+      __threadfence();  // this chunk's list is visible before the count says so
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = atomicAdd(plan.done + jj, 1) == nchunks - 1;
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        const int64_t M = (int64_t)nchunks * kappa;
+        const float* base = scores + a.off[jj];
+        const int64_t kap = kappa;
+        auto ent = [base, kap](int64_t e) { return base + (e / kap) * kChunk + (e % kap); };
+        const bool mc = M <= kFusedCache;
+        if (mc)
+          for (int64_t e = threadIdx.x; e < M; e += blockDim.x) kc[e] = score_key(__ldcg(ent(e)));
+        __syncthreads();
+        select_topk(
+            S, M, kappa, mc, [&](int64_t e) -> uint32_t { return mc ? kc[e] : score_key(__ldcg(ent(e))); },
+            [&](int64_t e) -> int32_t { return __ldcg(reinterpret_cast<const int32_t*>(ent(e) + kap)); },
+            out_s + jj * kappa, out_id + jj * kappa);
+      }
+    }
+    if (threadIdx.x == 0) {
+      cp_async_wait_all();
+      s_claimed = claim_ahead;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  if (MODE == 2 && threadIdx.x == 0 && abort_flag) report(a.d_status, GLV_ERR_TIMEOUT);
-  const float* sj = scores + p0;
-  const int32_t* ij = a.ids + p0;
-  select_topk(
-      S, L_, kappa, cached, [&](int64_t p) -> uint32_t { return cached ? kc[p] : score_key(sj[p]); },
-      [&](int64_t p) -> int32_t { return ij[p]; }, out_s + j * kappa, out_id + j * kappa);
 }
 
 // Set kernel k's preferred shared-memory carveout: carve_kb > 0 caps it (when one CTA of
@@ -195,24 +279,30 @@ struct ScoreLaunch {
 
 struct FusedLaunch {
   const ScoreArgs& a;
-  int64_t nq;
-  int RB;
+  unsigned grid;
   int kappa;
+  ChunkPlan plan;
+  int direct;
   float* out_s;
   int32_t* out_id;
   int carve_kb;
   cudaStream_t st;
   template <int DT, int G, int NCH, int MODE>
   cudaError_t go() {
-    auto k = score_topk_kernel<DT, G, NCH, MODE>;
-    const size_t smem = score_smem(a.C, a.qstride, true, MODE, RB, a.nch, kappa).total();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = apply_carveout(reinterpret_cast<const void*>(k), smem, carve_kb);
-    if (e != cudaSuccess) return e;
-    k<<<(unsigned)nq, kScoreThreads, smem, st>>>(a, RB, kappa, out_s, out_id);
-    return cudaGetLastError();
-  }};
+    if constexpr (MODE == 2) {
+      return cudaErrorInvalidValue;  // the launcher maps the bulk gather to register loads
+    } else {
+      auto k = score_topk_kernel<DT, G, NCH, MODE>;
+      const size_t smem = score_smem(a.C, a.qstride, true, MODE, 0, a.nch, kappa).total();
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      e = apply_carveout(reinterpret_cast<const void*>(k), smem, carve_kb);
+      if (e != cudaSuccess) return e;
+      k<<<grid, kScoreThreads, smem, st>>>(a, kappa, plan, direct, out_s, out_id);
+      return cudaGetLastError();
+    }
+  }
+};
 
 template <int DT>
 cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, int RB, ScoreConfig cfg, cudaStream_t st) {
@@ -221,16 +311,16 @@ cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, int RB, ScoreConfig c
 }
 
 template <int DT>
-cudaError_t launch_fused_dt(const ScoreArgs& a, int64_t nq, int RB, int kappa, float* out_s, int32_t* out_id,
-                            ScoreConfig cfg, cudaStream_t st) {
-  FusedLaunch f{a, nq, RB, kappa, out_s, out_id, cfg.carve_kb, st};
-  return dispatch_score<DT>(cfg.G, a.nch, cfg.mode, f);
+cudaError_t launch_fused_dt(const ScoreArgs& a, unsigned grid, int kappa, const ChunkPlan& plan, float* out_s,
+                            int32_t* out_id, ScoreConfig cfg, cudaStream_t st) {
+  FusedLaunch f{a, grid, kappa, plan, cfg.sched == 0 ? 1 : 0, out_s, out_id, cfg.carve_kb, st};
+  return dispatch_score<DT>(cfg.G, a.nch, cfg.mode == 2 ? 0 : cfg.mode, f);
 }
 
 #define GLV_INSTANTIATE_SCORE_PLAIN(DT) \
   template cudaError_t launch_score_dt<DT>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
-#define GLV_INSTANTIATE_SCORE_FUSED(DT)                                                            \
-  template cudaError_t launch_fused_dt<DT>(const ScoreArgs&, int64_t, int, int, float*, int32_t*, \
+#define GLV_INSTANTIATE_SCORE_FUSED(DT)                                                                \
+  template cudaError_t launch_fused_dt<DT>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*, int32_t*, \
                                            ScoreConfig, cudaStream_t);
 
 }  // namespace glv

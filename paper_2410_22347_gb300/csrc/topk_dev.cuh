@@ -4,7 +4,7 @@
 //
 // Scores are mapped to order-preserving uint32 keys; a 4-pass radix select (8-bit digits,
 // most significant first) finds the kappa-th largest key K*.  Every key above K* is taken;
-// among keys equal to K* the smallest ids are taken, found by a second radix select on ~id
+// among keys equal to K* the smallest ids are taken, found by a second radix select on id_rank(id)
 // only when the tie group is larger than what is left.  Histograms use warp-aggregated
 // shared-memory atomics (__match_any_sync), since similar scores pile into one bucket.
 //
@@ -18,7 +18,7 @@
 //
 // The kappa winners are sorted by (key desc, id asc).  After a filtered selection, up to 256
 // of them go through a bitonic network across the CTA's threads on the packed 64-bit value
-// key << 32 | ~id (exchanging through the key-cache region, free by then); otherwise each
+// key << 32 | id_rank(id) (exchanging through the key-cache region, free by then); otherwise each
 // entry counts the entries that rank before it.
 #pragma once
 
@@ -137,13 +137,13 @@ GLV_DEV void select_unordered(TopkSmem& S, int64_t L, int kappa, KeyOf key_of, I
   const bool all_ties = (S.n_eq == need_eq);
   if (!all_ties) {
     uint32_t rem2 = 0;
-    id_cut = radix_select(S, L, need_eq, [&](int64_t p) { return ~(uint32_t)id_of(p); },
+    id_cut = radix_select(S, L, need_eq, [&](int64_t p) { return id_rank(id_of(p)); },
                           [&](int64_t p) { return key_of(p) == kstar; }, &rem2);
   }
   for (int64_t p = threadIdx.x; p < L; p += blockDim.x) {
     if (key_of(p) != kstar) continue;
     const int32_t id = id_of(p);
-    if (all_ties || ~(uint32_t)id >= id_cut) {
+    if (all_ties || id_rank(id) >= id_cut) {
       const uint32_t slot = atomicAdd(&S.count, 1u);
       if (slot < (uint32_t)kappa) {  // only repeated (id, score) pairs can overflow
         S.sel_key[slot] = kstar;
@@ -199,7 +199,7 @@ GLV_DEV bool filter_to_region(TopkSmem& S, int64_t L, int kappa, uint32_t T, Key
   return S.fill >= (uint32_t)kappa && S.fill <= (uint32_t)cap;
 }
 
-// Sort the n (<= 256) selected pairs by (key desc, id asc) -- the packed value key << 32 | ~id
+// Sort the n (<= 256) selected pairs by (key desc, id asc) -- the packed value key << 32 | id_rank(id)
 // descending -- with a bitonic network over the first P = 2^ceil(log2 n) threads of the CTA,
 // one element per thread: partners closer than 32 are exchanged by warp shuffles, farther ones
 // through xs (256 slots of shared memory that are free at this point).  Writes out_s / out_id.
@@ -207,7 +207,7 @@ GLV_DEV void block_sort_write(TopkSmem& S, int n, uint64_t* xs, float* out_s, in
   const int t = threadIdx.x;
   int P = 2;
   while (P < n) P <<= 1;
-  uint64_t v = t < n ? ((uint64_t)S.sel_key[t] << 32) | (uint32_t)(~(uint32_t)S.sel_id[t]) : 0ull;
+  uint64_t v = t < n ? ((uint64_t)S.sel_key[t] << 32) | id_rank(S.sel_id[t]) : 0ull;
   for (int size = 2; size <= P; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       uint64_t o = 0;
@@ -228,17 +228,18 @@ GLV_DEV void block_sort_write(TopkSmem& S, int n, uint64_t* xs, float* out_s, in
   }
   if (t < n) {
     out_s[t] = key_score((uint32_t)(v >> 32));
-    out_id[t] = (int32_t)(~(uint32_t)v);
+    out_id[t] = id_from_rank((uint32_t)v);
   }
 }
 
-// Select and write the sorted top kappa of L candidates: key_of(p) / id_of(p) give the key
-// and id of candidate p in [0, L); `in_region` says whether the keys are the ones cached in
-// S.region (else S.region is free).  Writes kappa (score, id) pairs to out_s / out_id, padded
-// with (-inf, -1).  All threads of the CTA must call it.
+// Select and write the top kappa of L candidates: key_of(p) / id_of(p) give the key and id
+// of candidate p in [0, L); `in_region` says whether the keys are the ones cached in S.region
+// (else S.region is free).  Writes kappa (score, id) pairs to out_s / out_id, sorted and
+// padded with (-inf, -1); with sorted == false, writes the min(L, kappa) selected pairs in no
+// particular order (a partial list for a later merge).  All threads of the CTA must call it.
 template <class KeyOf, class IdOf>
 GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, bool in_region, KeyOf key_of, IdOf id_of,
-                         float* out_s, int32_t* out_id) {
+                         float* out_s, int32_t* out_id, bool sorted = true) {
   if (threadIdx.x == 0) {
     S.count = 0;
     S.n_eq = 0;
@@ -270,8 +271,37 @@ GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, bool in_region, KeyO
   }
   __syncthreads();
   const int n = min((int)S.count, kappa);
+  if (!sorted) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      out_s[e] = key_score(S.sel_key[e]);
+      out_id[e] = S.sel_id[e];
+    }
+    return;
+  }
   if (!in_region && n <= 256 && S.region_words >= 512 && blockDim.x >= 256) {
     block_sort_write(S, n, reinterpret_cast<uint64_t*>(S.region), out_s, out_id);
+  } else if (n <= S.region_words / 2) {
+    // place by rank on the packed value key << 32 | id_rank(id) (descending = key desc, id
+    // asc),
+    // staged in the key-cache region (free now); identical entries are ordered by slot so
+    // every rank is written once
+    uint64_t* xs = reinterpret_cast<uint64_t*>(S.region);
+    for (int e = threadIdx.x; e < n; e += blockDim.x)
+      xs[e] = ((uint64_t)S.sel_key[e] << 32) | id_rank(S.sel_id[e]);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const uint64_t ce = xs[e];
+      int above = 0, dup = 0;
+#pragma unroll 4
+      for (int f = 0; f < n; ++f) {
+        const uint64_t cf = xs[f];
+        above += cf > ce ? 1 : 0;
+        dup += (cf == ce && f < e) ? 1 : 0;
+      }
+      const int rank = above + dup;
+      out_s[rank] = key_score((uint32_t)(ce >> 32));
+      out_id[rank] = id_from_rank((uint32_t)ce);
+    }
   } else {
     // place by rank; identical entries are ordered by slot so every rank is written once
     for (int e = threadIdx.x; e < n; e += blockDim.x) {

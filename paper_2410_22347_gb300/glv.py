@@ -48,11 +48,12 @@ def _load() -> ctypes.CDLL:
         "glv_project_queries_workspace_size": (sz, [i64, i32, i32, i32, i32]),
         "glv_project_queries": (i32, [P, i64, i32, P, i32, i32, i32, P, P, P, P]),
         "glv_score_candidates": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P]),
-        "glv_score_topk": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, i32, P, P, P, P, P]),
+        "glv_score_topk_workspace_size": (sz, [i64, i64]),
+        "glv_score_topk": (i32, [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, i64, i32, P, P, P, P, P, P]),
         "glv_topk": (i32, [P, P, P, i64, i32, P, P, P]),
         "glv_score_lazy": (i32, [P, i64, i32, P, i32, i32, P, i64, P, i32, P, i64, P, P, P, P, P, P]),
-        "glv_set_score_config": (i32, [i32, i32, i32, i32]),
-        "glv_get_score_config": (i32, [i32, i32, P, P, P]),
+        "glv_set_score_config": (i32, [i32, i32, i32, i32, i32]),
+        "glv_get_score_config": (i32, [i32, i32, P, P, P, P]),
         "glv_rerank": (i32, [P, i64, i32, P, i64, P, i32, i32, P, P, P, P]),
         "glv_gather_rows": (i32, [P, i64, i64, P, i64, P, P, P]),
     }
@@ -246,8 +247,12 @@ def glv_score_lazy(Q, A, Xred, row_stride: int, scales, dt: int, tags, off, ids,
     return scores, visited
 
 
+def score_topk_workspace_bytes(nq: int, n_candidates: int) -> int:
+    return int(_lib.glv_score_topk_workspace_size(int(nq), int(n_candidates)))
+
+
 def glv_score_topk(Qp, Xred, row_stride: int, scales, dt: int, tags, off, ids, kappa: int, scores_scratch=None,
-                   out_s=None, out_id=None, d_status=None, stream=None, d: int | None = None):
+                   out_s=None, out_id=None, d_status=None, stream=None, d: int | None = None, workspace=None):
     """Fused scoring + top-kappa (same results as glv_score_candidates then glv_topk)."""
     _need(Qp, torch.float32, "Qp", 3)
     _need(tags, torch.uint16, "tags", 1)
@@ -256,16 +261,19 @@ def glv_score_topk(Qp, Xred, row_stride: int, scales, dt: int, tags, off, ids, k
     nq, C, dq = Qp.shape
     d = dq if d is None else d
     N = tags.shape[0]
+    n_cand = ids.shape[0]
     if scores_scratch is None:
-        scores_scratch = torch.empty(max(ids.shape[0], 1), dtype=torch.float32, device=Qp.device)
+        scores_scratch = torch.empty(max(n_cand, 1), dtype=torch.float32, device=Qp.device)
+    if workspace is None:
+        workspace = torch.empty(max(score_topk_workspace_bytes(nq, n_cand), 1), dtype=torch.uint8, device=Qp.device)
     if out_s is None:
         out_s = torch.empty(nq, kappa, dtype=torch.float32, device=Qp.device)
     if out_id is None:
         out_id = torch.empty(nq, kappa, dtype=torch.int32, device=Qp.device)
     _check("glv_score_topk",
            _lib.glv_score_topk(_ptr(Qp), nq, C, d, _ptr(Xred), row_stride, _ptr(scales), dt, _ptr(tags), N,
-                               _ptr(off), _ptr(ids), kappa, _ptr(scores_scratch), _ptr(out_s), _ptr(out_id),
-                               _ptr(d_status), _stream(stream)))
+                               _ptr(off), _ptr(ids), n_cand, kappa, _ptr(scores_scratch), _ptr(workspace),
+                               _ptr(out_s), _ptr(out_id), _ptr(d_status), _stream(stream)))
     return out_s, out_id
 
 
@@ -278,20 +286,22 @@ GATHER_MODES = (0, 1, 2)  # registers, registers pipelined, bulk copies into sha
 # about 92 KB of the SM's 256 KB to L1 for the rows in flight)
 SCORE_CARVEOUTS = (0, 164)
 
+# fused-call schedules: 1 = planned work items (long lists cut into chunks), 0 = one CTA per query
+SCORE_SCHEDULES = (1, 0)
 
-def glv_set_score_config(dt: int, lanes_per_candidate: int, gather_mode: int, smem_carveout_kb: int = 0) -> None:
+
+def glv_set_score_config(dt: int, lanes_per_candidate: int, gather_mode: int, smem_carveout_kb: int = 0,
+                         schedule: int = 1) -> None:
     _check("glv_set_score_config", _lib.glv_set_score_config(dt, int(lanes_per_candidate), int(gather_mode),
-                                                              int(smem_carveout_kb)))
+                                                              int(smem_carveout_kb), int(schedule)))
 
 
-def glv_get_score_config(dt: int, d: int) -> tuple[int, int, int]:
-    """(lanes per candidate, gather mode, carveout cap KB) used for rows of width d."""
-    g = ctypes.c_int32(0)
-    p = ctypes.c_int32(0)
-    c = ctypes.c_int32(0)
+def glv_get_score_config(dt: int, d: int) -> tuple[int, int, int, int]:
+    """(lanes per candidate, gather mode, carveout cap KB, fused schedule) used for rows of width d."""
+    g, p, c, h = (ctypes.c_int32(0) for _ in range(4))
     _check("glv_get_score_config", _lib.glv_get_score_config(dt, int(d), ctypes.byref(g), ctypes.byref(p),
-                                                              ctypes.byref(c)))
-    return int(g.value), int(p.value), int(c.value)
+                                                              ctypes.byref(c), ctypes.byref(h)))
+    return int(g.value), int(p.value), int(c.value), int(h.value)
 
 
 def glv_topk(scores, off, ids, kappa: int, out_s=None, out_id=None, stream=None):

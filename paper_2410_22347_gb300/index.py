@@ -49,6 +49,7 @@ class GleanVecIndex:
                 pws=torch.empty(max(glv.project_workspace_bytes(nq, self.D, self.C, self.d, self.compute), 1),
                                 dtype=torch.uint8, device=dev),
                 scores=torch.empty(max(total, 1), dtype=torch.float32, device=dev),
+                tws=torch.empty(max(glv.score_topk_workspace_bytes(nq, total), 1), dtype=torch.uint8, device=dev),
                 ts=torch.empty(nq, kappa, dtype=torch.float32, device=dev),
                 ti=torch.empty(nq, kappa, dtype=torch.int32, device=dev),
                 fs=torch.empty(nq, k, dtype=torch.float32, device=dev),
@@ -67,11 +68,13 @@ class GleanVecIndex:
                                 stream=stream)
         if kappa <= 0:
             glv.glv_score_topk(b["Qp"], self.Xred, self.row_stride, self.scales, self.dt, self.tags, off, ids, k,
-                               scores_scratch=b["scores"], out_s=b["fs"], out_id=b["fi"], d_status=self.status,
+                               scores_scratch=b["scores"], workspace=b["tws"], out_s=b["fs"], out_id=b["fi"],
+                               d_status=self.status,
                                stream=stream)
             return b["fs"], b["fi"]
         glv.glv_score_topk(b["Qp"], self.Xred, self.row_stride, self.scales, self.dt, self.tags, off, ids, kappa,
-                           scores_scratch=b["scores"], out_s=b["ts"], out_id=b["ti"], d_status=self.status,
+                           scores_scratch=b["scores"], workspace=b["tws"], out_s=b["ts"], out_id=b["ti"],
+                           d_status=self.status,
                            stream=stream)
         glv.glv_rerank(self.X, Q, b["ti"], k, out_s=b["fs"], out_id=b["fi"], d_status=self.status,
                        stream=stream)

@@ -53,7 +53,7 @@ def _ret_i32(lib, name, argtypes):
 def test_host_validation_rejects_bad_arguments(lib):
     i64, i32 = ctypes.c_int64, ctypes.c_int32
     lib.glv_abi_version.restype = i32
-    assert lib.glv_abi_version() == 2
+    assert lib.glv_abi_version() == 4
     lib.glv_min_row_stride.restype = i64
     lib.glv_min_row_stride.argtypes = [i32, i32]
     assert lib.glv_min_row_stride(160, 0) == 640
@@ -113,6 +113,21 @@ def test_host_validation_rejects_bad_arguments(lib):
     # FP32 (TF32 hi/lo): K padded to 128; Q 100 x 128 x 4 B and A 16 x 128 x 4 B, two copies each
     assert lib.glv_project_queries_workspace_size(100, 100, 2, 8, 0) == 2 * 51200 + 2 * 8192
 
+    lib.glv_score_topk_workspace_size.restype = ctypes.c_size_t
+    lib.glv_score_topk_workspace_size.argtypes = [i64, i64]
+    # header 256 B + chunk_start (nq + 1) + done (nq) + a 24-byte record per work item (one per
+    # query and per 4096 candidates, plus one), each array rounded to 256 bytes
+    r256 = lambda b: (b + 255) // 256 * 256
+    assert lib.glv_score_topk_workspace_size(10000, 20480000) == \
+        256 + r256(10001 * 4) + r256(10000 * 4) + r256((10000 + 5000 + 1) * 24)
+    stk = _ret_i32(lib, "glv_score_topk", [P, i64, i32, i32, P, i64, P, i32, P, i64, P, P, i64, i32, P, P, P, P, P, P])
+    args = [FAKE, 700, 4, 16, FAKE, 64, None, 0, FAKE, 10, FAKE, FAKE, 1000, 10, FAKE]
+    assert stk(*args, None, FAKE, FAKE, None, None) == INV              # no workspace
+    assert stk(*args, P(4096 + 16), FAKE, FAKE, None, None) == INV      # misaligned workspace
+    bad = list(args)
+    bad[12] = -1
+    assert stk(*bad, FAKE, FAKE, FAKE, None, None) == INV               # negative candidate count
+
     tags = _ret_i32(lib, "glv_assign_tags", [P, i64, i32, P, i32, P, P, P])
     assert tags(FAKE, 10, 8, FAKE, 0, FAKE, None, None) == INV
     assert tags(FAKE, 10, 2048, FAKE, 4, FAKE, None, None) == 3          # D beyond the kernel's limit
@@ -121,20 +136,21 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert lib.glv_status_string(2) == b"id or tag out of range"
 
     # scoring configuration: host-only state, checked without a GPU
-    setc = _ret_i32(lib, "glv_set_score_config", [i32, i32, i32, i32])
-    getc = _ret_i32(lib, "glv_get_score_config", [i32, i32, P, P, P])
-    g, m, c = i32(0), i32(0), i32(0)
-    ref = [ctypes.byref(x) for x in (g, m, c)]
-    assert setc(1, 4, 1, 164) == 0
-    assert getc(1, 160, *ref) == 0 and (g.value, m.value, c.value) == (4, 1, 164)
-    assert setc(1, 4, 1, 8) == INV          # carveout cap below 16 KB
-    assert setc(1, 4, 1, 300) == INV        # above the SM's shared memory
-    assert setc(1, 3, 0, 0) == INV          # lanes per candidate not a power of two
-    assert setc(1, 4, 3, 0) == INV          # no gather mode 3
-    assert setc(5, 4, 0, 0) == INV          # unknown store type
+    setc = _ret_i32(lib, "glv_set_score_config", [i32, i32, i32, i32, i32])
+    getc = _ret_i32(lib, "glv_get_score_config", [i32, i32, P, P, P, P])
+    g, m, c, h = i32(0), i32(0), i32(0), i32(0)
+    ref = [ctypes.byref(x) for x in (g, m, c, h)]
+    assert setc(1, 4, 1, 164, 0) == 0
+    assert getc(1, 160, *ref) == 0 and (g.value, m.value, c.value, h.value) == (4, 1, 164, 0)
+    assert setc(1, 4, 1, 8, 1) == INV       # carveout cap below 16 KB
+    assert setc(1, 4, 1, 300, 1) == INV     # above the SM's shared memory
+    assert setc(1, 3, 0, 0, 1) == INV       # lanes per candidate not a power of two
+    assert setc(1, 4, 3, 0, 1) == INV       # no gather mode 3
+    assert setc(1, 4, 0, 0, 2) == INV       # no schedule 2
+    assert setc(5, 4, 0, 0, 1) == INV       # unknown store type
     assert getc(1, 160, None, *ref[1:]) == INV
-    assert setc(1, 0, 0, 0) == 0
-    assert getc(1, 160, *ref) == 0 and c.value == 0
+    assert setc(1, 0, 0, 0, 1) == 0
+    assert getc(1, 160, *ref) == 0 and c.value == 0 and h.value == 1
 
 
 def test_product_path_has_no_oracle_dependency():

@@ -434,11 +434,18 @@ def test_score_topk_fused_matches_separate(glv, dt_name, nq, kappa):
     dt = glv.DTYPES[dt_name]
     rng, X, Q, mu, A, B, tags = _problem(nq + kappa, N=17000, D=96, d=40, C=7, nq=nq)
     lens = rng.integers(0, 3000, nq)
-    # empty, single, exactly kappa, the on-chip key-cache edge, and long lists whose scores
-    # spill to the scratch (the selection filters them through the sample threshold)
+    # empty, single, exactly kappa, the on-chip key-cache edge, long lists whose scores spill
+    # to the scratch (the selection filters them through the sample threshold), and lists cut
+    # into 2 and 4 work items (8192 and 16500 candidates) whose chunk lists are merged
     lens[:7] = [0, 1, kappa, 2048, 2049, 5000, 16500]
+    lens[10] = 8192
     lists = _ragged_lists(rng, nq, len(X), lens)
     lists[7] = np.concatenate([lists[7][:10], [len(X) + 5]])  # a bad id
+    # bad ids score -inf and tie there: ties go to the smaller (signed) id, so negative ids
+    # come first; list 8's -inf group straddles kappa, list 9 is shorter than kappa
+    bad = np.concatenate([-np.arange(1, 121), len(X) + np.arange(130)])
+    lists[8] = np.concatenate([lists[8][:max(kappa // 2, 1)], rng.permutation(bad)])
+    lists[9] = np.array([-5, 7, len(X) + 5])
     off, ids = _csr(lists)
     st = _status()
     Xt, tt = _t(X), _t(tags)
@@ -554,12 +561,14 @@ def test_fused_matches_separate_in_every_gather_mode(glv, dt_name, mode, gi):
 def test_score_config_roundtrip(glv):
     try:
         glv.glv_set_score_config(glv.GLV_BF16, 8, 1)
-        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, 1, 0)
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, 1, 0, 1)
         # 8 lanes x 5 pipelined loads cannot cover a 160-chunk row: falls back to a default
-        g, m, _ = glv.glv_get_score_config(glv.GLV_BF16, 1280)
+        g, m, _, _ = glv.glv_get_score_config(glv.GLV_BF16, 1280)
         assert m == 0
-        glv.glv_set_score_config(glv.GLV_BF16, 4, 2, 164)
-        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (4, 2, 164)
+        glv.glv_set_score_config(glv.GLV_BF16, 4, 2, 164, 0)
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (4, 2, 164, 0)
+        with pytest.raises(glv.GlvError):
+            glv.glv_set_score_config(glv.GLV_BF16, 4, 0, 0, 2)
         with pytest.raises(glv.GlvError):
             glv.glv_set_score_config(glv.GLV_BF16, 3, 0)
         with pytest.raises(glv.GlvError):
@@ -571,15 +580,16 @@ def test_score_config_roundtrip(glv):
 
 
 @pytest.mark.parametrize("dt_name", ["bf16", "fp8"])
-def test_carveout_cap_changes_no_result(glv, dt_name):
-    """The carveout cap changes only the shared-memory / L1 split: scores and selections stay
-    bit-identical."""
+@pytest.mark.parametrize("kappa", [100, 1024])
+def test_carveout_and_schedule_change_no_result(glv, dt_name, kappa):
+    """The carveout cap changes only the shared-memory / L1 split, the schedule only how work
+    is spread over CTAs: scores and selections stay bit-identical (long lists included)."""
     dt = glv.DTYPES[dt_name]
     try:
-        glv.glv_set_score_config(dt, 0, 0, 0)
-        test_score_topk_fused_matches_separate(glv, dt_name, 700, 100)
-        glv.glv_set_score_config(dt, 0, 0, 164)
-        test_score_topk_fused_matches_separate(glv, dt_name, 700, 100)
+        for carve in (0, 164):
+            for sched in (1, 0):
+                glv.glv_set_score_config(dt, 0, 0, carve, sched)
+                test_score_topk_fused_matches_separate(glv, dt_name, 700, kappa)
     finally:
         glv.glv_set_score_config(dt, 0, 0)
 
