@@ -4,15 +4,39 @@
 // One CTA per query; q_j is staged in shared memory.  Each warp scores R survivors at a
 // time: every lane issues its 16-byte loads of all R rows (a D-float row is D/128 loads per
 // lane) before the FMAs, so a warp has R * D * 4 bytes in flight; shuffles finish the dots.
-// The k best are placed by rank ((score desc, id asc)), exact and sort-free.
+// The k best (score desc, id asc) come from a bitonic sort of the packed values
+// key << 32 | id_rank(id) in one warp (kappa <= 256), else each survivor's rank is counted.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "topk_dev.cuh"
 
 namespace glv {
 
 constexpr int kRerankThreads = 256;
 
-
+// Warp 0: sort the kappa (<= 32 E) scored survivors, invalid ones packed as 0 (last), and
+// write the first min(n_valid, k).
+template <int E>
+GLV_DEV void rerank_warp_topk(const RerankArgs& a, const uint32_t* skey, const int32_t* sid, const uint8_t* sval,
+                              int n, int64_t j) {
+  const int lane = threadIdx.x & 31;
+  uint64_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int t = lane * E + e;
+    v[e] = (t < a.kappa && sval[t]) ? ((uint64_t)skey[t] << 32) | id_rank(sid[t]) : 0ull;
+  }
+  warp_bitonic_sort<E>(v, lane);
+  const int m = n < a.k ? n : a.k;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int t = lane * E + e;
+    if (t < m) {
+      a.out_s[j * a.k + t] = key_score((uint32_t)(v[e] >> 32));
+      a.out_id[j * a.k + t] = id_from_rank((uint32_t)v[e]);
+    }
+  }
+}
 
 // VEC: D % 4 == 0 and X, Q 16-byte aligned -> float4 loads; NL = max float4 loads per lane
 // per row (D <= 128 * NL), R = rows per warp iteration.
@@ -103,6 +127,13 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const RerankArgs
   }
   __syncthreads();
   const int n = n_valid;
+  if (a.kappa <= 256) {
+    if (warp == 0) {
+      if (a.kappa <= 64) rerank_warp_topk<2>(a, skey, sid, sval, n, j);
+      else if (a.kappa <= 128) rerank_warp_topk<4>(a, skey, sid, sval, n, j);
+      else rerank_warp_topk<8>(a, skey, sid, sval, n, j);
+    }
+  } else {
   for (int e = threadIdx.x; e < a.kappa; e += blockDim.x) {
     if (!sval[e]) continue;
     const uint32_t ke = skey[e];
@@ -118,6 +149,7 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const RerankArgs
       a.out_s[j * a.k + rank] = key_score(ke);
       a.out_id[j * a.k + rank] = ie;
     }
+  }
   }
   for (int e = n + threadIdx.x; e < a.k; e += blockDim.x) {
     a.out_s[j * a.k + e] = -INFINITY;

@@ -199,6 +199,43 @@ GLV_DEV bool filter_to_region(TopkSmem& S, int64_t L, int kappa, uint32_t T, Key
   return S.fill >= (uint32_t)kappa && S.fill <= (uint32_t)cap;
 }
 
+// Descending bitonic network over 32 E packed values held E per lane (element i = lane * E +
+// j) in one warp; sizes and strides are template parameters, so every register index is a
+// compile-time constant.
+template <int E, int SIZE, int STRIDE>
+GLV_DEV void warp_bitonic_stage(uint64_t (&v)[E], int lane) {
+  if constexpr (STRIDE < E) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if ((j & STRIDE) == 0) {
+        const int jl = j | STRIDE;
+        const bool desc = ((lane * E + j) & SIZE) == 0;
+        const uint64_t x = v[j], y = v[jl];
+        const bool swap = desc ? (x < y) : (x > y);
+        v[j] = swap ? y : x;
+        v[jl] = swap ? x : y;
+      }
+    }
+  } else {
+    constexpr int lx = STRIDE / E;
+    const bool lower = (lane & lx) == 0;
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, v[j], lx);
+      const bool desc = ((lane * E + j) & SIZE) == 0;
+      const uint64_t mx = v[j] > o ? v[j] : o, mn = v[j] > o ? o : v[j];
+      v[j] = (lower == desc) ? mx : mn;
+    }
+  }
+  if constexpr (STRIDE > 1) warp_bitonic_stage<E, SIZE, STRIDE / 2>(v, lane);
+}
+
+template <int E, int SIZE = 2>
+GLV_DEV void warp_bitonic_sort(uint64_t (&v)[E], int lane) {
+  warp_bitonic_stage<E, SIZE, SIZE / 2>(v, lane);
+  if constexpr (SIZE < 32 * E) warp_bitonic_sort<E, SIZE * 2>(v, lane);
+}
+
 // Sort the n (<= 256) selected pairs by (key desc, id asc) -- the packed value key << 32 | id_rank(id)
 // descending -- with a bitonic network over the first P = 2^ceil(log2 n) threads of the CTA,
 // one element per thread: partners closer than 32 are exchanged by warp shuffles, farther ones
