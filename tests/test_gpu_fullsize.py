@@ -1,0 +1,103 @@
+"""Parity at the benchmark's full size, in the launch configuration the benchmark times.
+
+Workload graph-1M-d160 (1M x 768 database, d = 160, C = 32, 10,000 OOD queries with 2,048
+random candidates each, kappa = 100 -> k = 10): the public search path (tcgen05 projection ->
+fused score + top-kappa -> re-rank) runs over all 10,000 queries, and sampled queries are
+checked against the oracle one by one:
+
+* the fused top-kappa: the oracle scores every candidate of the query in FP64 from the GPU's
+  own reduced rows (the stored codes, decoded exactly) and the GPU's projected query, and its
+  top-kappa must equal the GPU's up to ties within the FP32 accumulation error; the GPU's
+  top-kappa scores must match the oracle's within 1e-5 of the Cauchy-Schwarz scale;
+* the re-rank: the oracle's exact FP64 top-k of the GPU's survivors must equal the GPU's
+  final top-k up to ties, with scores within 1e-5.
+
+Reduced rows and projected queries are taken from the GPU because their own rounding (BF16 /
+FP8 codes, BF16 projection operands) is checked by the parity tests of those steps; here the
+question is whether the timed path computes the scores, selections and re-rank exactly at the
+benchmark's size and launch shape.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle.compare import scores_close, topk_equivalent
+
+pytestmark = pytest.mark.gpu
+
+SAMPLE = 8
+
+
+@pytest.fixture(scope="module")
+def workload():
+    from paper_2410_22347_gb300 import build_lib
+    build_lib.build()
+    from paper_2410_22347_gb300 import synth
+    w = synth.workload("graph-1M-d160", device=torch.device("cuda", 0))
+    yield w
+    del w
+    torch.cuda.empty_cache()
+
+
+def _decoded_rows(glv, ix, rows):
+    """FP64 values of the stored reduced rows `rows` (their codes, decoded exactly)."""
+    raw = ix.Xred[torch.from_numpy(rows).to(ix.Xred.device).long()].cpu().numpy()
+    d = ix.d
+    if ix.dt == glv.GLV_F32:
+        return raw.view(np.float32)[:, :d].astype(np.float64)
+    if ix.dt == glv.GLV_BF16:
+        return oracle.bf16_decode(raw.view(np.uint16)[:, :d])
+    sc = ix.scales[torch.from_numpy(rows).to(ix.Xred.device).long()].cpu().numpy()
+    return oracle.dequantize_fp8_rows(raw[:, :d], sc)
+
+
+@pytest.mark.parametrize("store", ["bf16", "fp8", "f32"])
+def test_graph_1m_d160_sampled_queries_match_oracle(workload, store):
+    from paper_2410_22347_gb300 import glv
+    from paper_2410_22347_gb300.index import GleanVecIndex
+    w = workload
+    nq = w.Q.shape[0]
+    ix = GleanVecIndex(w.X, w.A, w.B, mu=w.mu, store=store)
+    fs, fi = ix.search(w.Q, w.off, w.ids, w.kappa, w.k)
+    torch.cuda.synchronize()
+    assert ix.device_status() == 0
+    b = ix._buffers(nq, w.ids.shape[0], max(w.kappa, w.k), w.k)
+    ts, ti = b["ts"].cpu().numpy(), b["ti"].cpu().numpy()
+    fs, fi = fs.cpu().numpy(), fi.cpu().numpy()
+    off = w.off.cpu().numpy()
+    all_tags = ix.tags.cpu().numpy()
+    rng = np.random.default_rng(4242)
+    for j in np.sort(rng.choice(nq, SAMPLE, replace=False)):
+        lst = w.ids[int(off[j]):int(off[j + 1])].cpu().numpy()
+        tags = all_tags[lst]
+        xr = _decoded_rows(glv, ix, lst)
+        qp = b["Qp"][j:j + 1].cpu().numpy().astype(np.float64)
+        loc_off = np.array([0, len(lst)], np.int64)
+        s_ref, _ = oracle.score(qp, xr, tags, loc_off, np.arange(len(lst), dtype=np.int32))
+        # FP32 accumulation error bound of this query's scores (Cauchy-Schwarz scale)
+        cs = np.linalg.norm(qp[0][tags], axis=1) * np.linalg.norm(xr, axis=1)
+        window = 2e-5 * cs.max()
+        ref_s, ref_id = oracle.topk(s_ref, loc_off, lst.astype(np.int32), w.kappa)
+        by_id = dict(zip(lst.tolist(), s_ref.tolist()))
+        ok, why = topk_equivalent(ti[j], ref_id[0], ref_s[0], lambda i: by_id[i], window)
+        assert ok, f"{store} query {j} top-kappa: {why}"
+        pos = {int(i): t for t, i in enumerate(lst)}
+        ok, err, bad = scores_close(ts[j], [by_id[int(i)] for i in ti[j]], [cs[pos[int(i)]] for i in ti[j]])
+        assert ok, f"{store} query {j} top-kappa scores: worst {err} at {bad[:5]}"
+        # re-rank of the GPU's survivors: exact FP64 <q, x> over D
+        surv = ti[j:j + 1].astype(np.int32)
+        xs = w.X[torch.from_numpy(surv[0]).to(w.X.device).long()].cpu().numpy()
+        q = w.Q[j:j + 1].cpu().numpy()
+        ex = xs.astype(np.float64) @ q[0].astype(np.float64)
+        rr_s, rr_id, _ = oracle.rerank(xs, q, np.arange(w.kappa, dtype=np.int32)[None, :], w.k)
+        rr_id_g = surv[0][rr_id[0]]
+        exact = dict(zip(surv[0].tolist(), ex.tolist()))
+        win = 2e-5 * np.linalg.norm(q[0]) * np.linalg.norm(xs, axis=1).max()
+        ok, why = topk_equivalent(fi[j], rr_id_g, rr_s[0], lambda i: exact[i], win)
+        assert ok, f"{store} query {j} re-rank: {why}"
+        scale = np.linalg.norm(q[0]) * np.linalg.norm(xs, axis=1).max()
+        ok, err, bad = scores_close(fs[j], [exact[int(i)] for i in fi[j]], scale)
+        assert ok, f"{store} query {j} re-rank scores: worst {err}"
+    del ix
+    torch.cuda.empty_cache()
