@@ -62,6 +62,11 @@ GLV_DEV void cp_async8(void* smem_dst, const void* gsrc) {
 }
 GLV_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Hint: bring `bytes` (a multiple of 16) at the 16-byte aligned global address p into L2.
+GLV_DEV void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Ids as unsigned keys that grow as the (signed) id shrinks: ties between equal scores go to
 // the smaller id, negative (invalid) ids included, in every selection path.
 GLV_DEV uint32_t id_rank(int32_t id) { return ~((uint32_t)id ^ 0x80000000u); }

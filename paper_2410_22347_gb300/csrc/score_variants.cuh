@@ -160,6 +160,20 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
   float* scores = a.scores;
   for (int cur = 0;; cur ^= 1) {
     if (!s_valid[cur]) break;
+    // thread 0: copy the next item's record into the other slot (it lands during this item's
+    // gather) and claim the item after it
+    if (threadIdx.x == 0) {
+      const int claimed = s_claimed;
+      const bool has_nxt = claimed < s_items;
+      s_valid[cur ^ 1] = has_nxt;
+      if (has_nxt) {
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(plan.items + claimed);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&s_rec[cur ^ 1]);
+#pragma unroll
+        for (int w = 0; w < (int)(sizeof(ItemRec) / 8); ++w) cp_async8(dst + w, src + w);
+        s_claimed = atomicAdd(plan.next, 1);
+      }
+    }
     const int64_t j = s_rec[cur].q;
     if (j != s_staged) stage_qp<DT>(a, j, qs);
     __syncthreads();
@@ -172,24 +186,28 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
       auto sink = [scores](int64_t p, float s) { scores[p] = s; };
       score_range<DT, G, NCH, MODE == 1>(a, qs, b0, b1, sink);
     }
-    // thread 0: copy the next item's record into the other slot asynchronously and claim the
-    // item after it; both land while the current item is being selected (nothing here waits)
-    int claim_ahead = 0;
-    if (threadIdx.x == 0) {
-      const int claimed = s_claimed;
-      const bool has_nxt = claimed < s_items;
-      s_valid[cur ^ 1] = has_nxt;
-      if (has_nxt) {
-        const uint64_t* src = reinterpret_cast<const uint64_t*>(plan.items + claimed);
-        uint64_t* dst = reinterpret_cast<uint64_t*>(&s_rec[cur ^ 1]);
-#pragma unroll
-        for (int w = 0; w < (int)(sizeof(ItemRec) / 8); ++w) cp_async8(dst + w, src + w);
-        claim_ahead = atomicAdd(plan.next, 1);
-      } else {
-        claim_ahead = claimed;
+    if (threadIdx.x == 0) cp_async_wait_all();
+    __syncthreads();
+    // while this item is being selected, let DRAM fetch the start of the next one: its first
+    // rows (one per thread) and its query's projected views go to L2
+    if (s_valid[cur ^ 1]) {
+      const int64_t nb0 = s_rec[cur ^ 1].b0, nq = s_rec[cur ^ 1].q;
+      const int nlen = s_rec[cur ^ 1].len;
+      if (threadIdx.x < nlen) {
+        const int64_t id = a.ids[nb0 + threadIdx.x];
+        if (id >= 0 && id < a.N) prefetch_l2_bulk(a.Xred + id * a.row_stride, (uint32_t)a.row_stride);
+      }
+      const int64_t qbytes = (int64_t)a.C * a.d * 4;
+      if (nq != s_staged && (qbytes & 15) == 0) {
+        const int pieces = (int)((qbytes + 4095) / 4096);
+        const int t = (int)blockDim.x - 1 - (int)threadIdx.x;
+        if (t < pieces) {
+          const int64_t o = (int64_t)t * 4096;
+          prefetch_l2_bulk(reinterpret_cast<const uint8_t*>(a.Qp) + nq * qbytes + o,
+                           (uint32_t)(qbytes - o < 4096 ? qbytes - o : 4096));
+        }
       }
     }
-    __syncthreads();
     // re-read the item after the barrier (nothing of it stays live across the gather)
     const int nchunks = s_rec[cur].nchunks;
     const int64_t jj = s_rec[cur].q, c0 = s_rec[cur].b0, lc = s_rec[cur].len;
@@ -227,10 +245,6 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
             [&](int64_t e) -> int32_t { return __ldcg(reinterpret_cast<const int32_t*>(ent(e) + kap)); },
             out_s + jj * kappa, out_id + jj * kappa);
       }
-    }
-    if (threadIdx.x == 0) {
-      cp_async_wait_all();
-      s_claimed = claim_ahead;
     }
     __syncthreads();
   }
