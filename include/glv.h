@@ -64,6 +64,14 @@ typedef enum { GLV_F32 = 0, GLV_BF16 = 1, GLV_FP8_E4M3 = 2 } glv_dtype;
 int32_t glv_abi_version(void);
 const char* glv_status_string(glv_status s);
 
+/* ---------------------------------------------------------------------------------------
+ * Device-detected errors land in a caller-provided int32 status word (d_status arguments):
+ * 0 while nothing went wrong, else the first glv_status code recorded.  This helper waits
+ * for `stream` (cudaStreamSynchronize), reads the word and returns it (GLV_ERR_CUDA if the
+ * wait or the read fails, GLV_ERR_INVALID_ARG for a NULL word).  It does not reset it.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_last_device_status(const int32_t* d_status, void* stream);
+
 /* Smallest legal row stride in bytes of a reduced-row store of width d and type dt:
  * d * sizeof(element) rounded up to 16 bytes (rows are read with 16-byte vector loads). */
 int64_t glv_min_row_stride(int32_t d, glv_dtype dt);

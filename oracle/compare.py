@@ -25,7 +25,8 @@ def scores_close(got, ref, scale, tol=1e-5):
     ref = np.asarray(ref, np.float64)
     scale = np.broadcast_to(np.asarray(scale, np.float64), ref.shape)
     both_inf = np.isinf(got) & np.isinf(ref) & (np.sign(got) == np.sign(ref))
-    err = np.where(both_inf, 0.0, np.abs(got - ref))
+    with np.errstate(invalid="ignore"):  # inf - inf where both are the same infinity
+        err = np.where(both_inf, 0.0, np.abs(got - ref))
     lim = tol * np.maximum(np.abs(np.where(np.isinf(ref), 0.0, ref)), scale)
     bad = ~(err <= lim)
     return not bad.any(), (np.nanmax(err / np.maximum(lim / tol, 1e-300)) if err.size else 0.0), np.flatnonzero(bad)

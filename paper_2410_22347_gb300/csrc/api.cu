@@ -90,6 +90,14 @@ const char* glv_status_string(glv_status s) {
   return "unknown status";
 }
 
+glv_status glv_last_device_status(const int32_t* d_status, void* stream) {
+  GLV_CHECK(d_status != nullptr, GLV_ERR_INVALID_ARG);
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GLV_ERR_CUDA;
+  int32_t v = 0;
+  if (cudaMemcpy(&v, d_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return GLV_ERR_CUDA;
+  return (glv_status)v;
+}
+
 int64_t glv_min_row_stride(int32_t d, glv_dtype dt) {
   if (d <= 0 || !valid_dt(dt)) return -1;
   return ((int64_t)d * elem_bytes(dt) + 15) / 16 * 16;

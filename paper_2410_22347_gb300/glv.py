@@ -37,6 +37,7 @@ def _load() -> ctypes.CDLL:
     P, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
     sig = {
         "glv_abi_version": (i32, []),
+        "glv_last_device_status": (i32, [P, P]),
         "glv_status_string": (ctypes.c_char_p, [i32]),
         "glv_min_row_stride": (i64, [i32, i32]),
         "glv_assign_tags": (i32, [P, i64, i32, P, i32, P, P, P]),
@@ -73,6 +74,12 @@ def lib() -> ctypes.CDLL:
 
 def status_string(s: int) -> str:
     return _lib.glv_status_string(int(s)).decode()
+
+
+def glv_last_device_status(d_status, stream=None) -> int:
+    """Waits for the stream and returns the device status word (0 = no error recorded)."""
+    _need(d_status, torch.int32, "d_status", 1)
+    return int(_lib.glv_last_device_status(_ptr(d_status), _stream(stream)))
 
 
 def abi_version() -> int:

@@ -134,6 +134,8 @@ def test_host_validation_rejects_bad_arguments(lib):
 
     lib.glv_status_string.restype = ctypes.c_char_p
     assert lib.glv_status_string(2) == b"id or tag out of range"
+    lds = _ret_i32(lib, "glv_last_device_status", [P, P])
+    assert lds(None, None) == INV           # no status word: rejected before any CUDA call
 
     # scoring configuration: host-only state, checked without a GPU
     setc = _ret_i32(lib, "glv_set_score_config", [i32, i32, i32, i32, i32])

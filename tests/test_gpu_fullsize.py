@@ -101,3 +101,40 @@ def test_graph_1m_d160_sampled_queries_match_oracle(workload, store):
         assert ok, f"{store} query {j} re-rank scores: worst {err}"
     del ix
     torch.cuda.empty_cache()
+
+
+def test_exhaustive_10k_matches_oracle():
+    """The small plain-FP32 configuration end to end (exhaustive-10k: 10k x 512 database,
+    d = 128, C = 8, 100 OOD queries, every row a candidate, top 10 of the reduced scores, no
+    re-rank), through the public search path in the configuration the library picks for so
+    few queries (lists split over many CTAs, then the stand-alone top-k), against the FP64
+    oracle pipeline on the same cluster tags."""
+    from paper_2410_22347_gb300 import build_lib, synth
+    build_lib.build()
+    from paper_2410_22347_gb300.index import GleanVecIndex
+    w = synth.workload("exhaustive-10k", device=torch.device("cuda", 0))
+    ix = GleanVecIndex(w.X, w.A, w.B, mu=w.mu, store="f32", project="f32")
+    fs, fi = ix.search(w.Q, w.off, w.ids, 0, w.k)
+    torch.cuda.synchronize()
+    assert ix.device_status() == 0
+    X, Q, A, B = (t.cpu().numpy() for t in (w.X, w.Q, w.A, w.B))
+    off, ids = w.off.cpu().numpy(), w.ids.cpu().numpy()
+    tags = ix.tags.cpu().numpy()
+    # the GPU's tags are the oracle's except at near-ties (checked by the tag tests)
+    ref_tags, margin = oracle.assign_tags(X, w.mu.cpu().numpy(), return_margin=True)
+    assert np.all((tags == ref_tags) | (margin <= 1e-5))
+    qp = oracle.project(Q, A)
+    xr = oracle.build_reduced(X, tags, B)
+    s_ref, _ = oracle.score(qp, xr, tags, off, ids)
+    ref_s, ref_id = oracle.topk(s_ref, off, ids, w.k)
+    fs, fi = fs.cpu().numpy(), fi.cpu().numpy()
+    qn = np.linalg.norm(qp, axis=2)  # |q_c| per query and cluster
+    xn = np.linalg.norm(xr, axis=1)
+    for j in range(Q.shape[0]):
+        sj = s_ref[off[j]:off[j + 1]]  # every row is a candidate, in id order
+        scale = qn[j, tags] * xn
+        window = 2e-5 * scale.max()
+        ok, why = topk_equivalent(fi[j], ref_id[j], ref_s[j], lambda i: sj[i], window)
+        assert ok, f"query {j}: {why}"
+        ok, err, bad = scores_close(fs[j], sj[fi[j]], scale[fi[j]])
+        assert ok, f"query {j}: scores, worst {err}"

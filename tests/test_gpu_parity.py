@@ -285,6 +285,13 @@ def test_score_candidates_wide_rows_and_many_clusters(glv, dt_name):
     _score_case(glv, dt, 8, 24, 300, [1500, 20], N=1600, D=48)
 
 
+def test_last_device_status_reports_the_word(glv):
+    st = _status()
+    assert glv.glv_last_device_status(st) == 0
+    st.fill_(glv.GLV_ERR_BAD_ID)
+    assert glv.glv_last_device_status(st) == glv.GLV_ERR_BAD_ID
+
+
 def test_score_candidates_bad_ids_flagged(glv):
     _score_case(glv, glv.GLV_F32, 5, 32, 4, [20, 3], bad_ids=True)
 
