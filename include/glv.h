@@ -271,6 +271,28 @@ glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_cand
                                 int32_t* gather_mode, int32_t* smem_carveout_kb, int32_t* schedule);
 
 /* ---------------------------------------------------------------------------------------
+ * The whole eager multi-step search in one call (Algorithm 1 with Algorithm 4):
+ * glv_project_queries -> glv_score_topk (kappa survivors) -> glv_rerank (exact top k), or,
+ * with kappa == 0, the top k of the reduced scores without a re-rank.  Same arguments,
+ * results and errors as those calls, in that order; the intermediate arrays (projected
+ * queries, projection operands, score scratch, work plan, survivors) are carved from one
+ * caller-provided workspace of glv_search_workspace_size(nq, D, C, d, compute,
+ * n_candidates, kappa) bytes, 256-byte aligned, contents on entry irrelevant.
+ *   X : N x D float32 (the re-rank's rows);  Q : nq x D float32;  A : C x d x D float32.
+ *   compute : projection operands, GLV_F32 (3xTF32, FP32-accurate) or GLV_BF16.
+ *   Xred, row_stride, scales, dt, tags, cand_off, cand_ids, n_candidates : as for
+ *   glv_score_topk.   kappa : 0, or k <= kappa <= GLV_MAX_KAPPA.   out_s, out_id : nq x k.
+ * ------------------------------------------------------------------------------------- */
+size_t glv_search_workspace_size(int64_t nq, int32_t D, int32_t C, int32_t d, glv_dtype compute,
+                                 int64_t n_candidates, int32_t kappa);
+glv_status glv_search(const float* X, int64_t N, int32_t D, const float* Q, int64_t nq,
+                      const float* A, int32_t C, int32_t d, glv_dtype compute, const void* Xred,
+                      int64_t row_stride, const float* scales, glv_dtype dt, const uint16_t* tags,
+                      const int64_t* cand_off, const int32_t* cand_ids, int64_t n_candidates,
+                      int32_t kappa, int32_t k, void* workspace, float* out_s, int32_t* out_id,
+                      int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Gather calibration (no counterpart in the paper; a measuring instrument for the roofline
  * of the gather-score): for every entry p of ids, reads the whole row ids[p] of a row-major
  * store and writes out[p] = the row's 32-bit words summed as floats -- the same bytes in the

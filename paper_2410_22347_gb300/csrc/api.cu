@@ -356,3 +356,51 @@ glv_status glv_gather_rows(const void* rows, int64_t row_bytes, int64_t n_rows, 
                                 (cudaStream_t)stream));
   return GLV_OK;
 }
+
+// ---- one-call search: projection -> fused score + top-kappa -> re-rank ---------------------
+
+static size_t round_up256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t glv_search_workspace_size(int64_t nq, int32_t D, int32_t C, int32_t d, glv_dtype compute,
+                                 int64_t n_candidates, int32_t kappa) {
+  if (nq < 0 || D < 1 || C < 1 || d < 1 || n_candidates < 0 || kappa < 0) return 0;
+  size_t b = round_up256((size_t)nq * C * d * sizeof(float));                       // Qp
+  b += round_up256(glv_project_queries_workspace_size(nq, D, C, d, compute));        // operands
+  b += round_up256((size_t)(n_candidates > 0 ? n_candidates : 1) * sizeof(float));  // scratch
+  b += round_up256(glv_score_topk_workspace_size(nq, n_candidates));                 // plan
+  if (kappa > 0) b += round_up256((size_t)nq * kappa * 8);                           // survivors
+  return b;
+}
+
+glv_status glv_search(const float* X, int64_t N, int32_t D, const float* Q, int64_t nq, const float* A,
+                      int32_t C, int32_t d, glv_dtype compute, const void* Xred, int64_t row_stride,
+                      const float* scales, glv_dtype dt, const uint16_t* tags, const int64_t* cand_off,
+                      const int32_t* cand_ids, int64_t n_candidates, int32_t kappa, int32_t k, void* workspace,
+                      float* out_s, int32_t* out_id, int32_t* d_status, void* stream) {
+  GLV_CHECK(nq >= 0 && k >= 1 && kappa >= 0 && (kappa == 0 || kappa >= k), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(k <= GLV_MAX_KAPPA && kappa <= GLV_MAX_KAPPA && n_candidates >= 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(compute == GLV_F32 || compute == GLV_BF16, GLV_ERR_INVALID_ARG);
+  if (nq == 0) return GLV_OK;
+  GLV_CHECK(workspace && aligned(workspace, 256) && out_s && out_id, GLV_ERR_INVALID_ARG);
+  uint8_t* w = static_cast<uint8_t*>(workspace);
+  float* Qp = reinterpret_cast<float*>(w);
+  w += round_up256((size_t)nq * C * d * sizeof(float));
+  const size_t pws_bytes = glv_project_queries_workspace_size(nq, D, C, d, compute);
+  void* pws = pws_bytes ? static_cast<void*>(w) : nullptr;
+  w += round_up256(pws_bytes);
+  float* scratch = reinterpret_cast<float*>(w);
+  w += round_up256((size_t)(n_candidates > 0 ? n_candidates : 1) * sizeof(float));
+  void* tws = w;
+  w += round_up256(glv_score_topk_workspace_size(nq, n_candidates));
+  glv_status st = glv_project_queries(Q, nq, D, A, C, d, compute, Qp, pws, d_status, stream);
+  if (st != GLV_OK) return st;
+  if (kappa == 0)  // no re-rank: the top k of the reduced scores
+    return glv_score_topk(Qp, nq, C, d, Xred, row_stride, scales, dt, tags, N, cand_off, cand_ids, n_candidates, k,
+                          scratch, tws, out_s, out_id, d_status, stream);
+  float* surv_s = reinterpret_cast<float*>(w);
+  int32_t* surv_id = reinterpret_cast<int32_t*>(w + (size_t)nq * kappa * sizeof(float));
+  st = glv_score_topk(Qp, nq, C, d, Xred, row_stride, scales, dt, tags, N, cand_off, cand_ids, n_candidates, kappa,
+                      scratch, tws, surv_s, surv_id, d_status, stream);
+  if (st != GLV_OK) return st;
+  return glv_rerank(X, N, D, Q, nq, surv_id, kappa, k, out_s, out_id, d_status, stream);
+}

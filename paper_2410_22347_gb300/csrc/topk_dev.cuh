@@ -16,6 +16,11 @@
 // depends on the sample: when at least kappa keys are >= T, the kappa-th largest key is >= T
 // and every key that can be selected (ties included) is in the region.
 //
+// Lists whose keys are cached in the region with at most 8 per thread skip the block-wide
+// radix passes: a per-warp threshold (warp_threshold_filter) that provably leaves at least
+// kappa keys, one packing pass, and a rank count over the (typically 1.5 kappa, at most 256)
+// survivors, which writes the top kappa already sorted.  Wide tie groups take the radix path.
+//
 // The kappa winners are sorted by (key desc, id asc).  After a filtered selection, up to 256
 // of them go through a bitonic network across the CTA's threads on the packed 64-bit value
 // key << 32 | id_rank(id) (exchanging through the key-cache region, free by then); otherwise each
@@ -34,7 +39,7 @@ constexpr int kTopkCache = 8192;
 // 32-bit words, at least 512, 8-byte aligned) is the caller's key cache, reused as scratch.
 struct TopkSmem {
   uint32_t hist[256];
-  uint32_t bucket, above, count, n_eq, fill;
+  uint32_t bucket, above, count, n_eq, fill, thr;
   uint32_t* sel_key;
   int32_t* sel_id;
   uint32_t* region;
@@ -199,6 +204,120 @@ GLV_DEV bool filter_to_region(TopkSmem& S, int64_t L, int kappa, uint32_t T, Key
   return S.fill >= (uint32_t)kappa && S.fill <= (uint32_t)cap;
 }
 
+// Descending sort of 8 keys held in registers (a 19-comparator network).
+GLV_DEV void sort8_desc(uint32_t (&v)[8]) {
+  constexpr int kNet[19][2] = {{0, 2}, {1, 3}, {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}, {0, 1}, {2, 3},
+                               {4, 5}, {6, 7}, {2, 4}, {3, 5}, {1, 4}, {3, 6}, {1, 2}, {3, 4}, {5, 6}};
+#pragma unroll
+  for (int c = 0; c < 19; ++c) {
+    const uint32_t x = v[kNet[c][0]], y = v[kNet[c][1]];
+    v[kNet[c][0]] = max(x, y);
+    v[kNet[c][1]] = min(x, y);
+  }
+}
+
+// Keys cached in the region, at most kWarpThrKeys per thread (256 threads): a threshold T that
+// at least kappa of the L keys reach, found with one barrier.  Each warp pops the
+// r = ceil(kappa / 8) largest of its own keys (every lane's keys sorted in registers, one
+// warp max-reduction per pop), and T is the smallest of the eight warps' r-th largest keys,
+// so each warp holds r keys >= T and at least 8 r >= kappa list keys reach T (on random
+// scores about 1.5 kappa do).  One pass then packs every key >= T with its id
+// (key << 32 | id_rank(id)) into the region as 64-bit values and returns how many there are
+// (they hold the top kappa, ties included).  When that is more than one per thread (a wide
+// tie group), the keys are put back in the region and -1 is returned, for the radix path.
+// S.thr (all ones) and S.fill (0) are set by the caller before its barrier.
+constexpr int kWarpThrKeys = 8;
+
+template <class KeyOf, class IdOf>
+GLV_DEV int warp_threshold_filter(TopkSmem& S, int L, int kappa, KeyOf key_of, IdOf id_of) {
+  const int t = threadIdx.x, lane = t & 31;
+  uint32_t v[kWarpThrKeys];
+#pragma unroll
+  for (int i = 0; i < kWarpThrKeys; ++i) {
+    const int p = t + i * kTopkThreads;
+    v[i] = p < L ? key_of(p) : 0u;
+  }
+  sort8_desc(v);
+  const int r = (kappa + 7) / 8;
+  uint32_t tw = 0;
+  for (int s = 0; s < r; ++s) {
+    const uint32_t m = __reduce_max_sync(0xffffffffu, v[0]);
+    const bool win = lane == __ffs(__ballot_sync(0xffffffffu, v[0] == m)) - 1;
+#pragma unroll
+    for (int j = 0; j < kWarpThrKeys - 1; ++j) v[j] = win ? v[j + 1] : v[j];
+    v[kWarpThrKeys - 1] = win ? 0u : v[kWarpThrKeys - 1];
+    tw = m;
+  }
+  if (lane == 0) atomicMin(&S.thr, tw);
+  // the keys again, in list order (the sorted copy is spent), before the region is reused
+  uint32_t k[kWarpThrKeys];
+#pragma unroll
+  for (int i = 0; i < kWarpThrKeys; ++i) {
+    const int p = t + i * kTopkThreads;
+    k[i] = p < L ? key_of(p) : 0u;
+  }
+  __syncthreads();  // T is final, and every key is in registers: the region is free
+  const uint32_t T = S.thr;
+  uint32_t tot = 0;
+#pragma unroll
+  for (int i = 0; i < kWarpThrKeys; ++i)
+    tot += __popc(__ballot_sync(0xffffffffu, t + i * kTopkThreads < L && k[i] >= T));
+  uint32_t base = 0;
+  if (lane == 0 && tot) base = atomicAdd(&S.fill, tot);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t cap = kTopkThreads;
+  uint64_t* xs = reinterpret_cast<uint64_t*>(S.region);
+#pragma unroll
+  for (int i = 0; i < kWarpThrKeys; ++i) {
+    const bool pass = t + i * kTopkThreads < L && k[i] >= T;
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    if (pass) {
+      const uint32_t slot = base + __popc(bal & lt);
+      if (slot < cap) xs[slot] = ((uint64_t)k[i] << 32) | id_rank(id_of(t + i * kTopkThreads));
+    }
+    base += __popc(bal);
+  }
+  __syncthreads();
+  const uint32_t n = S.fill;
+  if (n <= cap) return (int)n;
+#pragma unroll
+  for (int i = 0; i < kWarpThrKeys; ++i) {
+    const int p = t + i * kTopkThreads;
+    if (p < L) S.region[p] = k[i];
+  }
+  __syncthreads();
+  return -1;
+}
+
+// The top kappa of n (kappa <= n <= blockDim.x) packed values xs, written sorted by (key
+// desc, id asc): entry t counts the entries that rank before it (identical entries ordered by
+// slot, so every rank is written once) and writes itself when its rank is below kappa.
+GLV_DEV void rank_place_packed(const uint64_t* xs, int n, int kappa, float* out_s, int32_t* out_id) {
+  const int t = threadIdx.x;
+  if (t >= n) return;
+  const uint64_t ce = xs[t];
+  int above = 0, dup = 0;
+  const ulonglong2* x2 = reinterpret_cast<const ulonglong2*>(xs);
+  const int n2 = n >> 1;
+#pragma unroll 4
+  for (int f = 0; f < n2; ++f) {
+    const ulonglong2 c = x2[f];
+    above += (c.x > ce ? 1 : 0) + (c.y > ce ? 1 : 0);
+    dup += (c.x == ce && 2 * f < t ? 1 : 0) + (c.y == ce && 2 * f + 1 < t ? 1 : 0);
+  }
+  if (n & 1) {
+    const uint64_t c = xs[n - 1];
+    above += c > ce ? 1 : 0;
+    dup += (c == ce && n - 1 < t) ? 1 : 0;
+  }
+  const int rank = above + dup;
+  if (rank < kappa) {
+    out_s[rank] = key_score((uint32_t)(ce >> 32));
+    out_id[rank] = id_from_rank((uint32_t)ce);
+  }
+}
+
 // Descending bitonic network over 32 E packed values held E per lane (element i = lane * E +
 // j) in one warp; sizes and strides are template parameters, so every register index is a
 // compile-time constant.
@@ -280,6 +399,8 @@ GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, bool in_region, KeyO
   if (threadIdx.x == 0) {
     S.count = 0;
     S.n_eq = 0;
+    S.fill = 0;
+    S.thr = 0xffffffffu;
   }
   __syncthreads();
   if (L <= kappa) {
@@ -290,7 +411,17 @@ GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, bool in_region, KeyO
     if (threadIdx.x == 0) S.count = (uint32_t)L;
   } else {
     bool done = false;
-    if (kappa <= kFilterMaxKappa && L >= kFilterMinList) {
+    if (in_region && L <= (int64_t)kWarpThrKeys * kTopkThreads && blockDim.x == kTopkThreads &&
+        kappa <= kFilterMaxKappa && S.region_words >= 512) {
+      const int n = warp_threshold_filter(S, (int)L, kappa, key_of, id_of);
+      const uint64_t* xs = reinterpret_cast<const uint64_t*>(S.region);
+      if (n >= 0) {
+        // kappa <= n <= blockDim.x: every rank below kappa is written
+        rank_place_packed(xs, n, kappa, out_s, out_id);
+        return;
+      }
+    }
+    if (!done && kappa <= kFilterMaxKappa && L >= kFilterMinList) {
       // lists cached on chip: the dense passes over shared memory are short, so they keep the
       // plain path (the threshold's extra barriers cost more latency than they save)
       const uint32_t T = in_region ? 0u : sample_threshold(S, L, kappa, key_of);

@@ -57,6 +57,9 @@ def _load() -> ctypes.CDLL:
         "glv_get_score_config": (i32, [i32, i32, P, P, P, P]),
         "glv_rerank": (i32, [P, i64, i32, P, i64, P, i32, i32, P, P, P, P]),
         "glv_gather_rows": (i32, [P, i64, i64, P, i64, P, P, P]),
+        "glv_search_workspace_size": (sz, [i64, i32, i32, i32, i32, i64, i32]),
+        "glv_search": (i32, [P, i64, i32, P, i64, P, i32, i32, i32, P, i64, P, i32, P, P, P, i64, i32, i32,
+                             P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -351,3 +354,30 @@ def glv_gather_rows(rows, row_bytes: int, ids, out=None, d_status=None, stream=N
     _check("glv_gather_rows", _lib.glv_gather_rows(_ptr(rows), int(row_bytes), n_rows, _ptr(ids), ids.shape[0],
                                                    _ptr(out), _ptr(d_status), _stream(stream)))
     return out
+
+
+def glv_search(X, Q, A, compute: int, Xred, row_stride: int, scales, dt: int, tags, off, ids, kappa: int, k: int,
+               workspace=None, out_s=None, out_id=None, d_status=None, stream=None):
+    """The whole search in one library call (projection -> fused score + top-kappa -> re-rank)."""
+    _need(X, torch.float32, "X", 2)
+    _need(Q, torch.float32, "Q", 2)
+    _need(A, torch.float32, "A", 3)
+    _need(tags, torch.uint16, "tags", 1)
+    _need(off, torch.int64, "cand_off", 1)
+    _need(ids, torch.int32, "cand_ids", 1)
+    N, D = X.shape
+    nq = Q.shape[0]
+    C, d, _ = A.shape
+    n_cand = ids.shape[0]
+    if workspace is None:
+        ws = int(_lib.glv_search_workspace_size(nq, D, C, d, compute, n_cand, kappa))
+        workspace = torch.empty(max(ws, 1), dtype=torch.uint8, device=Q.device)
+    if out_s is None:
+        out_s = torch.empty(nq, k, dtype=torch.float32, device=Q.device)
+    if out_id is None:
+        out_id = torch.empty(nq, k, dtype=torch.int32, device=Q.device)
+    _check("glv_search", _lib.glv_search(_ptr(X), N, D, _ptr(Q), nq, _ptr(A), C, d, compute, _ptr(Xred), row_stride,
+                                         _ptr(scales), dt, _ptr(tags), _ptr(off), _ptr(ids), n_cand, kappa, k,
+                                         _ptr(workspace), _ptr(out_s), _ptr(out_id), _ptr(d_status),
+                                         _stream(stream)))
+    return out_s, out_id

@@ -128,6 +128,30 @@ def test_host_validation_rejects_bad_arguments(lib):
     bad[12] = -1
     assert stk(*bad, FAKE, FAKE, FAKE, None, None) == INV               # negative candidate count
 
+    lib.glv_search_workspace_size.restype = ctypes.c_size_t
+    lib.glv_search_workspace_size.argtypes = [i64, i32, i32, i32, i32, i64, i32]
+    # Qp + projection operands + score scratch + work plan + kappa survivors, each 256-aligned
+    want = (r256(10000 * 32 * 160 * 4) + r256(10000 * 768 * 2 + 5120 * 768 * 2) + r256(20480000 * 4)
+            + r256(256 + r256(10001 * 4) + r256(10000 * 4) + r256((10000 + 5000 + 1) * 24)) + r256(10000 * 100 * 8))
+    assert lib.glv_search_workspace_size(10000, 768, 32, 160, 1, 20480000, 100) == want
+    assert lib.glv_search_workspace_size(10000, 768, 32, 160, 1, 20480000, 0) == want - r256(10000 * 100 * 8)
+    assert lib.glv_search_workspace_size(10, 0, 32, 160, 1, 100, 10) == 0        # D = 0
+    search = _ret_i32(lib, "glv_search", [P, i64, i32, P, i64, P, i32, i32, i32, P, i64, P, i32, P, P, P, i64,
+                                          i32, i32, P, P, P, P, P])
+    head = [FAKE, 1000, 64, FAKE, 5, FAKE, 4, 16, 1, FAKE, 64, None, 1, FAKE, FAKE, FAKE, 500]
+
+    def srch(kappa, k, ws=FAKE, compute=1, nq=5):
+        a = list(head)
+        a[4], a[8] = nq, compute
+        return search(*a, kappa, k, ws, FAKE, FAKE, None, None)
+    assert srch(8, 10) == INV               # kappa below k
+    assert srch(10, 0) == INV               # k = 0
+    assert srch(2000, 10) == INV            # kappa beyond the maximum
+    assert srch(20, 10, compute=2) == INV   # FP8 projection not offered
+    assert srch(20, 10, ws=None) == INV     # no workspace
+    assert srch(20, 10, ws=P(4096 + 64)) == INV  # misaligned workspace
+    assert srch(20, 10, nq=0) == 0          # no queries: nothing to do
+
     tags = _ret_i32(lib, "glv_assign_tags", [P, i64, i32, P, i32, P, P, P])
     assert tags(FAKE, 10, 8, FAKE, 0, FAKE, None, None) == INV
     assert tags(FAKE, 10, 2048, FAKE, 4, FAKE, None, None) == 3          # D beyond the kernel's limit

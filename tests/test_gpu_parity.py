@@ -324,13 +324,51 @@ def test_topk_exact(glv, kappa):
     np.testing.assert_array_equal(gs.astype(np.float64), ref_s)
 
 
-def test_topk_all_equal_scores(glv):
+@pytest.mark.parametrize("kappa", [100, 8, 256])
+def test_topk_all_equal_scores(glv, kappa):
+    # all-equal lists: beyond the key cache, cached with more tied keys than the packed
+    # survivors' room (2048, 2000, 1100), with a few hundred (300, 600), and a list whose
+    # 1500 largest scores are equal
     rng = _rng(3)
-    off, ids = _csr([rng.permutation(50000)[:12000], rng.permutation(50000)[:300]])
+    lens = [12000, 2048, 2000, 1100, 600, 300, 2000]
+    off, ids = _csr([rng.permutation(50000)[:L] for L in lens])
     s = np.ones(len(ids), np.float32)
-    ref_s, ref_id = oracle.topk(s.astype(np.float64), off, ids, 100)
-    gs, gi = glv.glv_topk(_t(s), _t(off), _t(ids), 100)
+    s[off[6]:off[6] + 500] = rng.standard_normal(500).astype(np.float32) - 5.0
+    ref_s, ref_id = oracle.topk(s.astype(np.float64), off, ids, kappa)
+    gs, gi = glv.glv_topk(_t(s), _t(off), _t(ids), kappa)
     np.testing.assert_array_equal(gi.cpu().numpy(), ref_id)
+    np.testing.assert_array_equal(gs.cpu().numpy().astype(np.float64), ref_s)
+
+
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("kappa", [100, 10, 256])
+def test_score_topk_fused_wide_ties(glv, dt_name, kappa):
+    """Rows repeat three patterns and the tags alternate, so a query's scores take a handful
+    of values and the kappa boundary falls inside tie groups of hundreds to thousands of candidates:
+    the fused top-kappa must take the smallest ids of the boundary group, as the oracle does."""
+    dt = glv.DTYPES[dt_name]
+    rng, X, Q, mu, A, B, _ = _problem(500 + kappa, N=9000, D=64, d=32, C=2, nq=9)
+    X = X[np.arange(len(X)) % 3]
+    tags = (np.arange(len(X)) % 2).astype(np.uint16)
+    lens = [2048, 2000, 1100, 700, 300, 130, 2049, 5000, 0]
+    off, ids = _csr(_ragged_lists(rng, 9, len(X), lens))
+    Xt, tt = _t(X), _t(tags)
+    Xred, scales = glv.glv_build_reduced(Xt, tt, _t(B), dt)
+    Qp = glv.glv_project_queries(_t(Q), _t(A), glv.GLV_F32)
+    rs = glv.min_row_stride(32, dt)
+    offt, idst = _t(off), _t(ids)
+    st = _status()
+    sc = glv.glv_score_candidates(Qp, Xred, rs, scales, dt, tt, offt, idst, d_status=st)
+    fs, fi = glv.glv_score_topk(Qp, Xred, rs, scales, dt, tt, offt, idst, kappa, d_status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    scn = sc.cpu().numpy()
+    # six (pattern, tag) values, each possibly in two roundings (the summation order of the
+    # low-precision gather depends on the candidate's slot)
+    assert len(np.unique(scn[off[0]:off[1]])) <= 12
+    ref_s, ref_id = oracle.topk(scn.astype(np.float64), off, ids, kappa)
+    np.testing.assert_array_equal(fi.cpu().numpy(), ref_id)
+    np.testing.assert_array_equal(fs.cpu().numpy().astype(np.float64), ref_s)
 
 
 # ---------------------------------------------------------------------------------------
@@ -502,6 +540,25 @@ def test_index_search_matches_oracle(glv):
     hs, hi = ix.search_host(w.Q.pin_memory(), w.off.pin_memory(), w.ids.pin_memory(), w.kappa, w.k)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(hi.numpy(), fi)
+
+
+@pytest.mark.parametrize("kappa", [0, 40])
+def test_one_call_search_matches_index_search(glv, kappa):
+    """glv_search (one C call, one workspace) gives exactly the results of the three calls."""
+    from paper_2410_22347_gb300 import synth
+    from paper_2410_22347_gb300.index import GleanVecIndex
+    w = synth.make_workload(N=30000, D=128, d=32, C=9, nq=700, K_db=12, cands=900, kappa=40, k=10, cfg=88)
+    X, Q, A, B, mu = (_t(t.numpy()) for t in (w.X, w.Q, w.A, w.B, w.mu))
+    off, ids = _t(w.off.numpy()), _t(w.ids.numpy())
+    ix = GleanVecIndex(X, A, B, mu=mu, store="bf16")
+    ws, wi = ix.search(Q, off, ids, kappa, w.k)
+    ws, wi = ws.cpu().numpy().copy(), wi.cpu().numpy().copy()
+    st = _status()
+    gs, gi = glv.glv_search(X, Q, ix.A, ix.compute, ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, off, ids,
+                            kappa, w.k, d_status=st)
+    assert glv.glv_last_device_status(st) == 0
+    np.testing.assert_array_equal(gi.cpu().numpy(), wi)
+    np.testing.assert_array_equal(gs.cpu().numpy().view(np.uint32), ws.view(np.uint32))
 
 
 def test_host_pipeline_matches_search(glv):
