@@ -11,13 +11,15 @@
 // multiple of 64 along K) into the caller's workspace; TMA then streams 128-byte-wide K
 // slices into shared memory in the 128-byte swizzled layout the MMA descriptors expect.
 //
-// Kernel structure (one persistent CTA per SM, 6 warps):
+// Kernel structure (one persistent CTA per SM, 10 warps):
 //   warp 0      TMA producer (one lane): stage ring of S slots, full/empty mbarriers;
 //   warp 1      TMEM owner + MMA issuer (one lane): 128 x 256 FP32 accumulator, double
 //               buffered in TMEM (2 x 256 columns) so the epilogue of tile t overlaps the
 //               MMAs of tile t+1;
-//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 32 columns at a time, transposed through a
-//               padded shared-memory tile -> coalesced FP32 global stores (128 B per row).
+//   warps 2..9  epilogue, two warps per TMEM lane quadrant (each half of the columns):
+//               tcgen05.ld 32 lanes x 32 columns at a time (the next chunk's load in flight
+//               while this one is stored), transposed through a padded shared-memory tile ->
+//               coalesced FP32 global stores (128 B per row).
 // Every mbarrier wait is bounded (see tc.cuh); a timeout sets GLV_ERR_TIMEOUT in d_status,
 // all roles leave their loops, outstanding TMA loads and MMAs are drained (bounded), and the
 // TMEM is freed before the CTA exits.
@@ -37,7 +39,8 @@ constexpr int kTcBM = 128;            // rows of Q per tile (MMA M)
 constexpr int kTcBN = 256;            // columns of Qp per tile (MMA N)
 constexpr int kTcRowBytes = 128;      // K slice per stage: one 128-byte swizzle row
 constexpr int kTcKpad = 64;           // operand rows padded to a multiple of 64 elements
-constexpr int kTcThreads = 192;
+constexpr int kTcEpiWarps = 8;      // two per TMEM lane quadrant, each storing half the columns
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
 
 template <int MODE>  // 0 = BF16, 1 = TF32x3
 struct TcCfg {
@@ -51,7 +54,7 @@ struct TcCfg {
   static constexpr int kKPerMma = MODE == 0 ? 16 : 8;     // 32 bytes of K per MMA
   static constexpr int kMmaPerStage = kKPerStage / kKPerMma;
   // epilogue staging: per epilogue warp a 32 x 32 FP32 tile, rows padded to 33 words
-  static constexpr size_t kEpiBytes = 4 * 32 * 33 * sizeof(float);
+  static constexpr size_t kEpiBytes = (size_t)kTcEpiWarps * 32 * 33 * sizeof(float);
   static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 + 256 + kEpiBytes;
 };
 
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&tfull[b], 1);
-      tc::mbar_init(&tempty[b], 128);
+      tc::mbar_init(&tempty[b], 32 * kTcEpiWarps);
     }
     tc::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -205,8 +208,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::mbar_wait(drain, 0, &no_abort);
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+    // ---------------- epilogue (warps 2..9) ----------------
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    constexpr int kChunks = kTcBN / 32 / (kTcEpiWarps / 4);  // 32-column chunks per warp
+    const int ch0 = ((warp - 2) / 4) * kChunks;
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int64_t t = blockIdx.x; t < args.num_tiles; t += gridDim.x) {
@@ -222,16 +227,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // lane = row in TMEM; each 32 x 32 chunk goes through the warp's shared-memory tile
       // (conflict-free: rows padded to 33 words) so the global stores write one row segment
       // of 32 consecutive columns (128 bytes) per instruction
+      // The TMEM load of the next chunk is issued once this chunk's values are in shared
+      // memory, so it lands while this chunk's global stores go out.
       float* stg = epi + (warp - 2) * (32 * 33);
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kTcBN + ch0 * 32);
+      uint32_t r[32];
+      tc::tmem_ld_32x32b_x32(tbase, r);
+      tc::tmem_ld_wait(r);
 #pragma unroll 1
-      for (int ch = 0; ch < kTcBN / 32; ++ch) {
-        uint32_t r[32];
-        tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kTcBN + ch * 32), r);
-        tc::tmem_ld_wait();
+      for (int ch = 0; ch < kChunks; ++ch) {
 #pragma unroll
         for (int u = 0; u < 32; ++u) stg[lane * 33 + u] = __uint_as_float(r[u]);
         __syncwarp();
-        const int64_t col = (int64_t)tn * kTcBN + ch * 32 + lane;
+        if (ch + 1 < kChunks) tc::tmem_ld_32x32b_x32(tbase + (uint32_t)((ch + 1) * 32), r);
+        const int64_t col = (int64_t)tn * kTcBN + (ch0 + ch) * 32 + lane;
         if (col < args.N) {
 #pragma unroll 8
           for (int rr = 0; rr < 32; ++rr) {
@@ -240,6 +249,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
         }
         __syncwarp();
+        tc::tmem_ld_wait(r);
       }
       tc::tc_fence_before();
       tc::mbar_arrive(&tempty[acc]);
