@@ -50,9 +50,9 @@ constexpr int fused_min_blocks_regs(int n) { return n <= 4 ? GLV_FUSED_MINB : n 
 
 // CTAs per SM the fused kernel is compiled for: the register budget must hold NCH row chunks
 // per lane (x2 when the next candidate's loads are in flight, mode 1) without spilling; the
-// FP8 decode costs about one chunk's worth of registers more.
+// FP8 decode costs about two chunks' worth of registers more.
 constexpr int fused_min_blocks(int dt, int mode, int nch) {
-  return mode == 2 ? 1 : mode == 1 ? 3 : fused_min_blocks_regs(nch + (dt == GLV_FP8_E4M3 ? 1 : 0));
+  return mode == 2 ? 1 : mode == 1 ? 3 : fused_min_blocks_regs(nch + (dt == GLV_FP8_E4M3 ? 2 : 0));
 }
 
 template <int DT, int G, int NCH, int MODE, class Sink>
