@@ -46,7 +46,7 @@ inline int bulk_rows(int C, int qstride, bool fused, int nch, int kappa, size_t 
 #define GLV_FUSED_MINB 6  // CTAs per SM the register-gather fused kernel is compiled for
 #endif
 
-constexpr int fused_min_blocks_regs(int n) { return n <= 4 ? GLV_FUSED_MINB : n <= 5 ? 5 : n <= 8 ? 4 : 3; }
+constexpr int fused_min_blocks_regs(int n) { return n <= 3 ? GLV_FUSED_MINB : n <= 5 ? 5 : n <= 8 ? 4 : 3; }
 
 // CTAs per SM the fused kernel is compiled for: the register budget must hold NCH row chunks
 // per lane (x2 when the next candidate's loads are in flight, mode 1) without spilling; the
