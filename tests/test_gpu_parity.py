@@ -542,15 +542,17 @@ def test_index_search_matches_oracle(glv):
     np.testing.assert_array_equal(hi.numpy(), fi)
 
 
-@pytest.mark.parametrize("kappa", [0, 40])
-def test_one_call_search_matches_index_search(glv, kappa):
-    """glv_search (one C call, one workspace) gives exactly the results of the three calls."""
+@pytest.mark.parametrize("store,kappa,nq", [("bf16", 0, 700), ("bf16", 40, 700), ("f32", 40, 700),
+                                            ("fp8", 40, 700), ("bf16", 40, 50)])
+def test_one_call_search_matches_index_search(glv, store, kappa, nq):
+    """glv_search (one C call, one workspace) gives exactly the results of the three calls
+    (FP32 store with the 3xTF32 projection; 50 queries take the split scoring path)."""
     from paper_2410_22347_gb300 import synth
     from paper_2410_22347_gb300.index import GleanVecIndex
-    w = synth.make_workload(N=30000, D=128, d=32, C=9, nq=700, K_db=12, cands=900, kappa=40, k=10, cfg=88)
+    w = synth.make_workload(N=30000, D=128, d=32, C=9, nq=nq, K_db=12, cands=900, kappa=40, k=10, cfg=88)
     X, Q, A, B, mu = (_t(t.numpy()) for t in (w.X, w.Q, w.A, w.B, w.mu))
     off, ids = _t(w.off.numpy()), _t(w.ids.numpy())
-    ix = GleanVecIndex(X, A, B, mu=mu, store="bf16")
+    ix = GleanVecIndex(X, A, B, mu=mu, store=store)
     ws, wi = ix.search(Q, off, ids, kappa, w.k)
     ws, wi = ws.cpu().numpy().copy(), wi.cpu().numpy().copy()
     st = _status()
