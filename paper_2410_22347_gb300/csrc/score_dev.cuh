@@ -113,6 +113,32 @@ GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
   constexpr int EPC = Elem<DT>::kPerChunk;
   const float* qj = a.Qp + j * (int64_t)a.C * a.d;
   const int dpad = a.nch * EPC;
+  if ((a.d & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Qp) & 15) == 0) {
+    // float4 at a time (the four elements of a float4 share a chunk and a sub-block slot),
+    // kU loads in flight per thread before their stores
+    constexpr int kU = 4;
+    const int q4 = dpad >> 2, total4 = a.C * q4;
+    for (int t0 = threadIdx.x; t0 < total4; t0 += kU * blockDim.x) {
+      float4 v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = t0 + u * blockDim.x;
+        const int c = t / q4, r = (t - c * q4) * 4;
+        v[u] = (t < total4 && r < a.d) ? *reinterpret_cast<const float4*>(qj + (int64_t)c * a.d + r)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < total4) {
+          const int c = t / q4, r = (t - c * q4) * 4;
+          const int ch = r / EPC, e = r - ch * EPC;
+          *reinterpret_cast<float4*>(qs + c * a.qstride + ((e >> 2) * a.sbs + ch) * 4) = v[u];
+        }
+      }
+    }
+    return;
+  }
   const int total = a.C * dpad;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int c = t / dpad, r = t - c * dpad;
