@@ -183,20 +183,30 @@ GLV_DEV bool filter_to_region(TopkSmem& S, int64_t L, int kappa, uint32_t T, Key
   if (threadIdx.x == 0) S.fill = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  for (int64_t b = 0; b < L; b += blockDim.x) {
-    const int64_t p = b + threadIdx.x;
-    const uint32_t k = p < L ? key_of(p) : 0u;
-    const bool pass = p < L && k >= T;
-    const unsigned bal = __ballot_sync(0xffffffffu, pass);
-    if (bal == 0) continue;
-    uint32_t base = 0;
-    if (lane == __ffs(bal) - 1) base = atomicAdd(&S.fill, (uint32_t)__popc(bal));
-    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-    if (pass) {
-      const uint32_t slot = base + __popc(bal & ((1u << lane) - 1u));
-      if (slot < (uint32_t)cap) {
-        bk[slot] = k;
-        bi[slot] = id_of(p);
+  // kU keys per thread are loaded before any is used, so their (L2) round trips overlap
+  constexpr int kU = 4;
+  for (int64_t b = 0; b < L; b += kU * blockDim.x) {
+    uint32_t kk[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t p = b + u * blockDim.x + threadIdx.x;
+      kk[u] = p < L ? key_of(p) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t p = b + u * blockDim.x + threadIdx.x;
+      const bool pass = p < L && kk[u] >= T;
+      const unsigned bal = __ballot_sync(0xffffffffu, pass);
+      if (bal == 0) continue;
+      uint32_t base = 0;
+      if (lane == __ffs(bal) - 1) base = atomicAdd(&S.fill, (uint32_t)__popc(bal));
+      base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+      if (pass) {
+        const uint32_t slot = base + __popc(bal & ((1u << lane) - 1u));
+        if (slot < (uint32_t)cap) {
+          bk[slot] = kk[u];
+          bi[slot] = id_of(p);
+        }
       }
     }
   }
