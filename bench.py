@@ -2,10 +2,23 @@
 """Benchmark of the GleanVec eager multi-step search on GB300.
 
 One step = one pass of the whole hot path over one batch of queries with device-resident
-inputs:  glv_project_queries -> glv_score_candidates -> glv_topk -> glv_rerank.
-Default workload: 1M x 768 database, d = 160, C = 32 clusters, 10,000 OOD queries, 2,048
-random candidate ids per query (graph-search-like gathers), kappa = 100 re-ranked to
-k = 10, reduced rows stored in BF16 (the FP32 store is timed beside it).
+inputs:  glv_project_queries -> glv_score_topk (fused scoring + top-kappa) -> glv_rerank.
+Headline workload (the line's value): graph-1M-d160 -- 1M x 768 database, d = 160, C = 32
+clusters, 10,000 OOD queries, 2,048 random candidate ids per query (graph-search-like
+gathers), kappa = 100 re-ranked to k = 10, reduced rows stored in BF16 (FP8 and FP32 stores
+timed beside it).  The default run also times, under "configs":
+
+* precision-10M-d128 -- 10M x 512, d = 128, C = 64, 10,000 OOD + 10,000 ID queries per step,
+  4,096 candidates each, kappa = 200: FP8 (one scale per row), BF16 and FP32 stores; recall
+  of the final top 10 against the FP64 oracle pipeline (R1) and against the exact top 10
+  over the candidates (R2); a kappa sweep, and each store's queries/s at the smallest kappa
+  whose R2 reaches 0.9 (the equal-recall comparison);
+* batching-2M-d192 -- 2M x 768, d = 192, C = 48, 8,192 queries with lognormal list lengths:
+  eager launches, the step as one CUDA-graph replay, and every query launched on its own.
+
+Every workload also reports its a0 build (glv_build_reduced) against the HBM roofline and
+the projection GEMM against the tensor peaks (BF16 from the driver's peaks file, TF32
+measured here with cuBLAS).
 
 Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): every rank holds a replica of the
 database and searches its own query set (queries are independent, so there is no data
@@ -33,24 +46,41 @@ sys.path.insert(0, ROOT)
 METRIC = "queries/s at 10-recall@10>=0.9 vs oracle (low-prec vs FP32); gather-score HBM GB/s"
 UNIT = "queries/s"
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
+HEADLINE = "graph-1M-d160"
+EXTRA_CONFIGS = ("precision-10M-d128", "batching-2M-d192")
+# (headline store, the other stores timed beside it) per workload
+STORES = {"graph-1M-d160": ("bf16", "fp8,f32"), "precision-10M-d128": ("fp8", "bf16,f32"),
+          "batching-2M-d192": ("bf16", ""), "exhaustive-10k": ("f32", "")}
+KAPPA_SWEEP = (10, 20, 50, 100, 200, 400, 800)
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
-    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="glv", choices=["glv", "reference"])
-    p.add_argument("--workload", default="graph-1M-d160")
-    p.add_argument("--store", default="bf16", choices=["f32", "bf16", "fp8"])
-    p.add_argument("--compare-stores", default="fp8,f32", help="comma list of other stores to time too")
+    p.add_argument("--workload", default=HEADLINE)
+    p.add_argument("--store", default=None, choices=["f32", "bf16", "fp8"])
+    p.add_argument("--compare-stores", default=None, help="comma list of other stores to time too ('none': none)")
+    p.add_argument("--configs", default="auto",
+                   help="comma list of further workloads timed under 'configs' ('auto': the precision and "
+                        "batching workloads when the headline workload runs without overrides; 'none')")
+    p.add_argument("--kappa-sweep", default="auto",
+                   help="comma list of re-rank depths to sweep ('auto': the precision workload's sweep)")
     p.add_argument("--cpu-sample", type=int, default=256, help="queries in the CPU-baseline sample")
     p.add_argument("--recall-sample", type=int, default=256)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-queries-per-step", type=int, default=256)
     p.add_argument("--no-autotune", action="store_true", help="keep the library's default scoring configuration")
-    p.add_argument("--graph", action="store_true", help="time the step as a captured CUDA graph")
-    p.add_argument("--queries", default="ood", choices=["ood", "id"], help="query distribution")
+    p.add_argument("--score-config", default=None,
+                   help="G/mode/carveout_kb/schedule: install this scoring configuration instead of autotuning")
+    p.add_argument("--graph", action="store_true", help="also time the step as a captured CUDA graph")
+    p.add_argument("--queries", default=None, choices=["ood", "id", "ood+id"],
+                   help="query distribution (default: the workload's own)")
     p.add_argument("--lazy", action="store_true",
                    help="also time the lazy inner product (Algorithm 3) against the eager path")
     p.add_argument("--score-error", action="store_true",
@@ -97,13 +127,17 @@ def job_throughput(per_rank_units: int, world: int, max_ms: float) -> float:
 
 
 def measured_peaks():
+    """Roofline denominators: the measured copy bandwidth and BF16 GEMM throughput on
+    the GB300s, else the recipe's fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             mp = json.load(f)
-        return float(mp["hbm_gbs"]), "measured"
+        return {"hbm_gbs": float(mp["hbm_gbs"]), "bf16_tflops": float(mp["bf16_tflops"]),
+                "bf16_tflops_sustained": float(mp.get("bf16_tflops_sustained", 0.0)) or None, "source": "measured"}
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS, "bf16_tflops_sustained": None,
+                "source": "fallback"}
 
 
 class ClockSampler:
@@ -182,46 +216,61 @@ KERNEL_SOURCES = tuple("paper_2410_22347_gb300/csrc/" + f for f in (
     "kernels.cuh", "score.cu", "score_bf16_fused.cu", "score_fp8_fused.cu", "score_f32_fused.cu"))
 
 
+# DRAM bytes per candidate of the fused score + top-kappa kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture, divided by the candidates of that launch), per
+# (workload, store), with the hash of the kernel sources the counters were taken with; the
+# summaries and the capture commands are in profiles/.  A row whose hash no longer matches
+# the sources gives traffic null.
+TRAFFIC = {
+    ("graph-1M-d160", "bf16"): ("2a38c4c7ee308f0d", 6.872470e9 / 20.48e6),
+}
+
+
 def recorded_traffic(workload: str, store: str):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, valid
-    only while the kernel source still has the hash the counters were taken with."""
-    path = os.path.join(ROOT, "profiles", "score_topk_traffic.md")
-    if not os.path.exists(path):
+    row = TRAFFIC.get((workload, store))
+    if row is None or row[0] != source_sha(*KERNEL_SOURCES):
         return None
-    sha = source_sha(*KERNEL_SOURCES)
-    with open(path) as f:
-        for line in f:
-            m = re.match(r"\s*traffic\s+(\S+)\s+(\S+)\s+([0-9a-f]+)\s+([0-9.eE+]+)", line)
-            if m and m.group(1) == workload and m.group(2) == store and m.group(3) == sha:
-                return float(m.group(4))
-    return None
+    return row[1]
 
 
 # ---------------------------------------------------------------------------------------
-# oracle (CPU baseline / reference arm / recall check) on a bounded sample
+# oracle (CPU baseline / reference arm / recall checks) on a bounded sample
 # ---------------------------------------------------------------------------------------
 
-def oracle_subproblem(X, Q, mu, A, B, off, ids, qsel):
-    """Restrict the problem to the database rows the selected queries touch (a valid
-    GleanVec problem on its own: tags and reduced rows are per row).  numpy inputs."""
+def oracle_subproblem(w, qsel):
+    """Restrict the problem to the database rows the selected queries touch (a valid GleanVec
+    problem on its own: tags and reduced rows are per row).  The rows are gathered where the
+    workload lives (on the GPU for the GPU arm), then copied to the host; the oracle computes
+    the cluster tags and reduced rows of the touched rows itself (timed as prep_s)."""
     import numpy as np
+    import torch
     import oracle
-    lists = [ids[off[j]:off[j + 1]] for j in qsel]
-    cat = np.concatenate(lists) if lists else np.zeros(0, np.int32)
-    uniq = np.unique(cat)
+    off = w.off.cpu().numpy()
+    qsel = np.asarray(qsel)
+    lists = [w.ids[int(off[j]):int(off[j + 1])] for j in qsel]
+    cat = torch.cat(lists) if lists else torch.zeros(0, dtype=torch.int32, device=w.ids.device)
+    uniq = torch.unique(cat)
+    lids = torch.searchsorted(uniq, cat).to(torch.int32)
+    Xs = w.X[uniq.long()].cpu().numpy()
+    Qs = w.Q[torch.as_tensor(qsel, device=w.Q.device).long()].cpu().numpy()
     loff = np.zeros(len(qsel) + 1, np.int64)
     loff[1:] = np.cumsum([len(l) for l in lists])
-    lids = np.searchsorted(uniq, cat).astype(np.int32)
-    Xs = np.ascontiguousarray(X[uniq])
     t0 = time.perf_counter()
-    tags = oracle.assign_tags(Xs, mu)
-    Xr = oracle.build_reduced(Xs, tags, B)
+    tags = oracle.assign_tags(Xs, w.mu.cpu().numpy())
+    Xr = oracle.build_reduced(Xs, tags, w.B.cpu().numpy())
     prep = time.perf_counter() - t0
-    return dict(X=Xs, Q=np.ascontiguousarray(Q[qsel]), A=A, tags=tags, Xr=Xr, off=loff, ids=lids, uniq=uniq,
-                prep_s=prep)
+    return dict(X=Xs, Q=Qs, A=w.A.cpu().numpy(), tags=tags, Xr=Xr, off=loff, ids=lids.cpu().numpy(),
+                uniq=uniq.cpu().numpy(), prep_s=prep)
+
+
+def _global(sp, ids):
+    import numpy as np
+    return np.where(ids >= 0, sp["uniq"][np.clip(ids, 0, None)], -1)
 
 
 def oracle_search_timed(sp, kappa, k, repeats=1):
+    """The oracle's whole search of the sample (project, score, top-kappa, re-rank), best of
+    `repeats` wall times; returns (seconds, final scores, final global ids)."""
     import oracle
     best = None
     out = None
@@ -231,9 +280,32 @@ def oracle_search_timed(sp, kappa, k, repeats=1):
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     s, i = out
-    import numpy as np
-    gid = np.where(i >= 0, sp["uniq"][np.clip(i, 0, None)], -1)
-    return best, s, gid
+    return best, s, _global(sp, i)
+
+
+def oracle_reduced_scores(sp):
+    import oracle
+    s, _ = oracle.score(oracle.project(sp["Q"], sp["A"]), sp["Xr"], sp["tags"], sp["off"], sp["ids"])
+    return s
+
+
+def oracle_final_ids(sp, red, kappa, k):
+    """Final top-k global ids of the oracle pipeline at re-rank depth kappa (0: no re-rank),
+    from its FP64 reduced scores `red`."""
+    import oracle
+    if kappa == 0:
+        _, ids = oracle.topk(red, sp["off"], sp["ids"], k)
+        return _global(sp, ids)
+    _, surv = oracle.topk(red, sp["off"], sp["ids"], kappa)
+    _, fid, _ = oracle.rerank(sp["X"], sp["Q"], surv, k)
+    return _global(sp, fid)
+
+
+def oracle_exact_ids(sp, k):
+    """Exact top-k of <q, x> over each sampled query's whole candidate list (global ids)."""
+    import oracle
+    _, ids = oracle.exact_topk(sp["X"], sp["Q"], sp["off"], sp["ids"], k)
+    return _global(sp, ids)
 
 
 # ---------------------------------------------------------------------------------------
@@ -245,20 +317,17 @@ def run_reference(args):
     if rank != 0:
         return 0
     import numpy as np
-    import torch
     import oracle
     from paper_2410_22347_gb300 import synth
 
     oracle.set_threads(os.cpu_count() or 1)
     w = synth.workload(args.workload, device="cpu", queries=args.queries, **args.overrides)
-    X, Q, mu, A, B = (t.numpy() for t in (w.X, w.Q, w.mu, w.A, w.B))
-    off, ids = w.off.numpy(), w.ids.numpy()
-    nq = Q.shape[0]
+    nq = w.Q.shape[0]
     per = min(args.ref_queries_per_step, nq)
     nsteps = args.warmup + args.steps
     sels = [np.arange(s * per, s * per + per) % nq for s in range(nsteps)]
     allq = np.unique(np.concatenate(sels))
-    sp = oracle_subproblem(X, Q, mu, A, B, off, ids, allq)
+    sp = oracle_subproblem(w, allq)
     pos = {int(q): t for t, q in enumerate(allq)}
     times = []
     for s in range(nsteps):
@@ -279,8 +348,8 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": args.workload, "queries_per_step": per, "candidates_per_query": 2048,
-                   "kappa": w.kappa, "k": w.k},
+        "config": {"workload": args.workload, "queries_per_step": per,
+                   "candidates_per_query": int(w.off[-1]) // nq, "kappa": w.kappa, "k": w.k},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                          "sample": f"{per} queries per step, reduced rows precomputed for the "
                                    f"{len(sp['uniq'])} rows they touch ({sp['prep_s']:.1f} s, untimed)"},
@@ -291,11 +360,520 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------------
+# GPU arm: building blocks
+# ---------------------------------------------------------------------------------------
+
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def search_step(glv, ix, w, b, kappa, ev=None):
+    """One step of the hot path over the whole batch: projection, fused score + top-kappa,
+    re-rank (kappa = 0: top k of the reduced scores, no re-rank)."""
+    if ev:
+        ev[0].record()
+    glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"], d_status=ix.status)
+    if ev:
+        ev[1].record()
+    kk = kappa if kappa > 0 else w.k
+    glv.glv_score_topk(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids, kk,
+                       scores_scratch=b["scores"], workspace=b["tws"], out_s=b["ts"] if kappa > 0 else b["fs"],
+                       out_id=b["ti"] if kappa > 0 else b["fi"], d_status=ix.status)
+    if ev:
+        ev[2].record()
+    if kappa > 0:
+        glv.glv_rerank(w.X, w.Q, b["ti"], w.k, out_s=b["fs"], out_id=b["fi"], d_status=ix.status)
+    if ev:
+        ev[3].record()
+    return b["fs"], b["fi"]
+
+
+def time_search(glv, ix, w, kappa, steps, warmup, flush, world, sampler=None, label=None):
+    """Times `steps` search steps with CUDA events on the launching stream (L2 evicted before
+    each step, outside the events); returns the per-step and per-kernel means."""
+    import torch
+    import torch.distributed as dist
+    nq = w.Q.shape[0]
+    total = int(w.off[-1])
+    b = ix._buffers(nq, total, max(kappa, w.k), w.k)
+    for _ in range(warmup):
+        search_step(glv, ix, w, b, kappa)
+    torch.cuda.synchronize()
+    evs = [_events(4) for _ in range(steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__enter__()
+    t0 = time.perf_counter()
+    if label:
+        torch.cuda.nvtx.range_push(label)  # lets a profiler select the timed launches
+    for s in range(steps):
+        flush.zero_()
+        search_step(glv, ix, w, b, kappa, evs[s])
+    if label:
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = None
+    if sampler:
+        sampler.__exit__()
+        clocks = sampler.summary()
+    if world > 1:
+        dist.barrier()
+    per_step = [evs[s][0].elapsed_time(evs[s][3]) for s in range(steps)]
+    kern = [[evs[s][t].elapsed_time(evs[s][t + 1]) for s in range(steps)] for t in range(3)]
+    tot_ms = max_over_ranks(sum(per_step))
+    assert ix.device_status() == 0, "device reported an error during the bench"
+    return dict(ms_per_step=tot_ms / steps, value=job_throughput(nq * steps, world, tot_ms),
+                kernels_ms={n: statistics.mean(v) for n, v in zip(("project", "score_topk", "rerank"), kern)},
+                wall_s=wall, clocks=clocks)
+
+
+def timed_ms(fn, flush, reps):
+    """Mean CUDA-event time of fn() over reps calls, L2 evicted before each."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = _events(2)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return sum(ms) / len(ms)
+
+
+def gather_ceiling_ms(glv, ix, w, flush):
+    """The same rows for the same candidate ids, read with no arithmetic (glv_gather_rows)."""
+    import torch
+    gout = torch.empty(int(w.off[-1]), dtype=torch.float32, device=w.ids.device)
+    ms = timed_ms(lambda: glv.glv_gather_rows(ix.Xred, ix.row_stride, w.ids, out=gout), flush, 10)
+    del gout
+    return ms
+
+
+def roofline_block(glv, ix, st, w, score_ms, gather_ms, peaks, name):
+    """HBM roofline of the fused score + top-kappa kernel: algorithmic bytes per launch (per
+    candidate: the reduced row's d elements, the FP8 row scale, the 4-byte id) over its
+    CUDA-event time, against the measured copy bandwidth."""
+    total = int(w.off[-1])
+    bpc = ix.d * glv.elem_bytes(ix.dt) + (4 if st == "fp8" else 0) + 4
+    alg = total * bpc
+    ach = alg / (score_ms / 1e3) / 1e9
+    gbytes = total * (ix.row_stride + 8)
+    hbm = peaks["hbm_gbs"]
+    tr = recorded_traffic(name, st)
+    return {"kernel": "glv_score_topk (score_topk_kernel)", "bound": "hbm", "achieved": ach, "peak": hbm,
+            "unit": "GB/s", "frac": ach / hbm, "peak_source": f"{peaks['source']} hbm_gbs",
+            "traffic": None if tr is None else tr * total, "algorithmic_bytes_per_launch": alg,
+            "bytes_per_candidate": bpc, "kernel_ms": score_ms,
+            "gather_ceiling": {"kernel": "glv_gather_rows (same rows, same ids, no arithmetic)", "ms": gather_ms,
+                               "achieved_GBs": gbytes / (gather_ms / 1e3) / 1e9,
+                               "frac_of_copy_peak": gbytes / (gather_ms / 1e3) / 1e9 / hbm,
+                               "score_topk_frac_of_ceiling": gather_ms / score_ms}}
+
+
+def build_block(glv, ix, w, flush, peaks):
+    """Time of the a0 build (glv_build_reduced) into the index's own store, and its HBM
+    roofline: X read once, tags, B, and the store (and FP8 scales) written."""
+    import torch
+    N, D = w.X.shape
+    C, d, _ = w.B.shape
+    ws = torch.empty(max(int(glv.lib().glv_build_reduced_workspace_size(N, C)), 1), dtype=torch.uint8,
+                     device=w.X.device)
+    ms = timed_ms(lambda: glv.glv_build_reduced(w.X, ix.tags, w.B, ix.dt, Xred=ix.Xred, row_stride=ix.row_stride,
+                                                scales=ix.scales, workspace=ws), flush, 3)
+    nbytes = N * D * 4 + N * 2 + C * d * D * 4 + N * ix.row_stride + (N * 4 if ix.scales is not None else 0)
+    ach = nbytes / (ms / 1e3) / 1e9
+    return {"kernel": "glv_build_reduced (grouping + build_gemm_kernel)", "ms": ms, "bound": "hbm",
+            "algorithmic_bytes": nbytes, "achieved": ach, "unit": "GB/s", "peak": peaks["hbm_gbs"],
+            "frac": ach / peaks["hbm_gbs"], "tflops": 2.0 * N * D * d / (ms / 1e3) / 1e12}
+
+
+def projection_block(glv, res, w, peaks, store_compute):
+    """Tensor roofline of the projection GEMM Qp = Q [A_1; ...; A_C]^T (its launches' event
+    time, operand preparation included): BF16 operands against the measured BF16 peak, the
+    FP32 mode (three TF32 MMAs per product) against the measured TF32 peak."""
+    nq, D = w.Q.shape
+    C, d, _ = w.A.shape
+    flops = 2.0 * nq * D * C * d
+    out = {}
+    for st, r in res.items():
+        ms = r["kernels_ms"]["project"]
+        if store_compute[st] == 1:
+            ach = flops / (ms / 1e3) / 1e12
+            out[st] = {"operands": "bf16", "ms": ms, "tflops": ach, "peak": peaks["bf16_tflops"],
+                       "frac": ach / peaks["bf16_tflops"], "peak_source": f"{peaks['source']} bf16_tflops"}
+        elif peaks.get("tf32_tflops"):
+            ach = 3 * flops / (ms / 1e3) / 1e12
+            out[st] = {"operands": "f32 as 3 TF32 products (hi*hi + hi*lo + lo*hi)", "ms": ms,
+                       "tf32_tflops_executed": ach, "peak": peaks["tf32_tflops"],
+                       "frac": ach / peaks["tf32_tflops"], "peak_source": "tf32 measured in this run (cuBLAS)"}
+    return out
+
+
+def measure_tf32_peak(dev):
+    """Dense TF32 throughput of cuBLAS on this GPU (8192^3, best of 10): the denominator of
+    the FP32-mode projection, which the driver's peaks file does not carry."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn(n, n, device=dev)
+        bm = torch.randn(n, n, device=dev)
+        for _ in range(3):
+            torch.matmul(a, bm)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(10):
+            e0, e1 = _events(2)
+            e0.record()
+            torch.matmul(a, bm)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def tune_block(glv, ix, w, kappa, args):
+    from paper_2410_22347_gb300.autotune import tune_score
+    if args.score_config:
+        G, mode, carve, sched = (int(x) for x in args.score_config.split("/"))
+        glv.glv_set_score_config(ix.dt, G, mode, carve, sched)
+        table = "given on the command line"
+    elif args.no_autotune:
+        G, mode, carve, sched = glv.glv_get_score_config(ix.dt, ix.d)
+        table = "library default"
+    else:  # untimed set-up: pick the scoring configuration for this store on this workload
+        G, mode, carve, sched, table = tune_score(ix, w.Q, w.off, w.ids, max(kappa, w.k), use_cache=False)
+    return {"lanes_per_candidate": G, "gather_mode": mode, "smem_carveout_kb": carve, "schedule": sched,
+            "ms_by_config(G/mode/carveout_kb/schedule)": table}
+
+
+def batching_block(glv, ix, w, args, flush, world, dev):
+    """The step as one CUDA-graph replay, and every query launched on its own."""
+    import torch
+    nq, D = w.Q.shape
+    C, d, _ = w.A.shape
+    total = int(w.off[-1])
+    kappa = w.kappa
+    b = ix._buffers(nq, total, kappa, w.k)
+    out = {}
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        search_step(glv, ix, w, b, kappa)  # warm the buffers on the capture stream
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        search_step(glv, ix, w, b, kappa)
+    gms = max_over_ranks(timed_ms(g.replay, flush, max(5, min(args.steps, 50))))
+    out["graph"] = {"ms_per_step": gms, "value": job_throughput(nq, world, gms)}
+    nsub = min(args.per_query or 1024, nq)
+    Qp1 = torch.empty(1, C, d, dtype=torch.float32, device=dev)
+    pws1 = torch.empty(max(glv.project_workspace_bytes(1, D, C, d, ix.compute), 1), dtype=torch.uint8, device=dev)
+    lib = glv.lib()
+    stv = glv._stream(None)
+
+    def one(j):
+        # every query on its own: projection, scoring + top-kappa, re-rank (pointer offsets)
+        lib.glv_project_queries(w.Q.data_ptr() + j * D * 4, 1, D, ix.A.data_ptr(), C, d, ix.compute,
+                                Qp1.data_ptr(), pws1.data_ptr(), None, stv)
+        lib.glv_score_topk(Qp1.data_ptr(), 1, C, d, ix.Xred.data_ptr(), ix.row_stride,
+                           None if ix.scales is None else ix.scales.data_ptr(), ix.dt, ix.tags.data_ptr(),
+                           ix.N, w.off.data_ptr() + j * 8, w.ids.data_ptr(), total, kappa,
+                           b["scores"].data_ptr(), b["tws"].data_ptr(), b["ts"].data_ptr() + j * kappa * 4,
+                           b["ti"].data_ptr() + j * kappa * 4, None, stv)
+        lib.glv_rerank(w.X.data_ptr(), ix.N, D, w.Q.data_ptr() + j * D * 4, 1,
+                       b["ti"].data_ptr() + j * kappa * 4, kappa, w.k,
+                       b["fs"].data_ptr() + j * w.k * 4, b["fi"].data_ptr() + j * w.k * 4, None, stv)
+
+    def all_one():
+        for j in range(nsub):
+            one(j)
+    pms = max_over_ranks(timed_ms(all_one, flush, 1))
+    out["per_query_launches"] = {"queries": nsub, "ms": pms, "value": job_throughput(nsub, world, pms)}
+    return out
+
+
+def e2e_block(glv, ix, w, args, world, flush):
+    """End to end through the host-buffer entry point (glv_search_host): every step copies
+    its queries and candidate lists from pinned host memory and reads its top k back, inside
+    the timed region.  Steps alternate over two streams (HostSearchPipeline), so one batch's
+    copies overlap the other's search; the serial figure is one batch alone on one stream."""
+    import torch
+    from paper_2410_22347_gb300.index import HostSearchPipeline
+    nq = w.Q.shape[0]
+    Qh = w.Q.cpu().pin_memory()
+    offh = w.off.cpu().pin_memory()
+    idsh = w.ids.cpu().pin_memory()
+    outs = torch.empty(nq, w.k, dtype=torch.float32, pin_memory=True)
+    outi = torch.empty(nq, w.k, dtype=torch.int32, pin_memory=True)
+    serial_ms = max_over_ranks(timed_ms(lambda: ix.search_host(Qh, offh, idsh, w.kappa, w.k, outs, outi), flush,
+                                        max(5, min(args.steps, 20))))
+    pipe = HostSearchPipeline(ix, w.kappa, w.k)
+    for _ in range(max(3, args.warmup)):
+        pipe.submit(Qh, offh, idsh, outs, outi)
+    pipe.synchronize()
+    steps = max(10, min(args.steps, 50))
+    e0, e1 = _events(2)
+    e0.record()
+    pipe.begin()
+    for _ in range(steps):
+        pipe.submit(Qh, offh, idsh, outs, outi)
+    pipe.end()
+    e1.record()
+    e1.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+    assert ix.device_status() == 0
+    h2d = Qh.numel() * 4 + offh.numel() * 8 + idsh.numel() * 4
+    d2h = outs.numel() * 4 + outi.numel() * 4
+    return {"value": job_throughput(nq, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+            "path": f"glv_search_host (C ABI, host buffers), {steps} steps over two streams (copies of one "
+                    f"batch overlap the search of the other); inputs larger than L2",
+            "serial_ms_per_batch": serial_ms}
+
+
+def query_kinds(w, name):
+    """(label, query index array) per query kind of the batch."""
+    import numpy as np
+    nq = w.Q.shape[0]
+    from paper_2410_22347_gb300 import synth
+    mix = synth.WORKLOADS.get(name, {}).get("queries", "ood")
+    if mix == "ood+id":
+        return [("ood", np.arange(nq // 2)), ("id", np.arange(nq // 2, nq))]
+    return [(mix, np.arange(nq))]
+
+
+def sample_queries(w, name, n, seed=12345):
+    """n queries drawn evenly from each query kind of the batch (sorted)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    kinds = query_kinds(w, name)
+    per = max(1, n // len(kinds))
+    sel = [np.sort(rng.choice(ix, size=min(per, len(ix)), replace=False)) for _, ix in kinds]
+    return np.concatenate(sel), [(lab, len(s)) for (lab, _), s in zip(kinds, sel)]
+
+
+def recall_by_kind(found, truth, counts):
+    import oracle
+    out, o = {}, 0
+    for lab, n in counts:
+        out[lab] = oracle.recall(found[o:o + n], truth[o:o + n])
+        o += n
+    out["all"] = oracle.recall(found, truth)
+    return out
+
+# ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
-def run_glv(args):
+def measure_workload(name, args, *, dev, rank, world, local, flush, peaks, stores, headline, overrides):
+    """Times one workload: every store's search step (autotuned), its fused kernel's roofline
+    and gather ceiling, its a0 build; on rank 0, recall of each store's final top 10 against
+    the FP64 oracle pipeline (R1) and against the exact top 10 over the candidates (R2); and,
+    where asked, a kappa sweep and the batching comparison."""
     import numpy as np
+    import torch
+    import oracle
+    from paper_2410_22347_gb300 import glv, synth
+    from paper_2410_22347_gb300.index import GleanVecIndex
+
+    w = synth.workload(name, device=dev, replica=rank, queries=args.queries if headline else None, **overrides)
+    nq, D = w.Q.shape
+    C, d, _ = w.A.shape
+    total = int(w.off[-1])
+    idx = {}
+    for st in stores:
+        first = next(iter(idx.values()), None)
+        idx[st] = GleanVecIndex(w.X, w.A, w.B, mu=w.mu if first is None else None,
+                                tags=None if first is None else first.tags, store=st)
+    torch.cuda.synchronize()
+    res, tuned, roof, builds = {}, {}, {}, {}
+    clocks = None
+    for si, st in enumerate(stores):
+        ix = idx[st]
+        tuned[st] = tune_block(glv, ix, w, w.kappa, args)
+        sampler = ClockSampler(local) if si == 0 else None
+        label = f"timed_{st}" if headline else f"timed_{name}_{st}"
+        r = time_search(glv, ix, w, w.kappa, args.steps, args.warmup, flush, world, sampler=sampler, label=label)
+        if si == 0:
+            clocks = r.pop("clocks")
+        else:
+            r.pop("clocks")
+        res[st] = r
+        roof[st] = roofline_block(glv, ix, st, w, r["kernels_ms"]["score_topk"], gather_ceiling_ms(glv, ix, w, flush),
+                                  peaks, name)
+        builds[st] = build_block(glv, ix, w, flush, peaks)
+    out = {"workload": name, "N": int(w.X.shape[0]), "D": D, "d": d, "C": C, "queries": nq,
+           "query_mix": synth.WORKLOADS.get(name, {}).get("queries", "ood") if not args.queries or not headline
+           else args.queries,
+           "candidates_per_query": total / nq, "candidates_per_query_max": int((w.off[1:] - w.off[:-1]).max()),
+           "kappa": w.kappa, "k": w.k, "clocks": clocks, "autotune": tuned, "build": builds,
+           "projection": projection_block(glv, res, w, peaks, {st: idx[st].compute for st in stores}),
+           "stores": {st: {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernels_ms": r["kernels_ms"],
+                           "roofline": roof[st]} for st, r in res.items()}}
+    out["_results"] = res
+    out["_launches_per_step"] = {st: 5 + (1 if tuned[st]["schedule"] == 1 else 0) for st in stores}
+
+    if name == "batching-2M-d192" or (headline and (args.graph or args.per_query)):
+        out["batching"] = batching_block(glv, idx[stores[0]], w, args, flush, world, dev)
+        out["batching"]["eager"] = {"ms_per_step": res[stores[0]]["ms_per_step"], "value": res[stores[0]]["value"]}
+
+    if headline and args.lazy:
+        ix = idx[stores[0]]
+        b = ix._buffers(nq, total, w.kappa, w.k)
+        vis = torch.empty(nq, dtype=torch.int32, device=dev)
+
+        def lazy_step():
+            glv.glv_score_lazy(w.Q, ix.A, ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids,
+                               scores=b["scores"], visited=vis)
+            glv.glv_topk(b["scores"], w.off, w.ids, w.kappa, out_s=b["ts"], out_id=b["ti"])
+
+        def eager_step():
+            glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"])
+            glv.glv_score_topk(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids, w.kappa,
+                               scores_scratch=b["scores"], workspace=b["tws"], out_s=b["ts"], out_id=b["ti"])
+        le, ee = timed_ms(lazy_step, flush, 10), timed_ms(eager_step, flush, 10)
+        out["lazy_vs_eager"] = {"lazy_ms": le, "eager_ms": ee, "visited_clusters_mean": float(vis.float().mean()),
+                                "visited_clusters_max": int(vis.max()), "clusters": C}
+
+    if headline:
+        out["e2e"] = e2e_block(glv, idx[stores[0]], w, args, world, flush)
+
+    # ---- recall against the FP64 oracle (rank 0, bounded sample) ----
+    if rank == 0:
+        oracle.set_threads(os.cpu_count() or 1)
+        qsel, counts = sample_queries(w, name, args.recall_sample)
+        sp = oracle_subproblem(w, qsel)
+        red = oracle_reduced_scores(sp)
+        exact = oracle_exact_ids(sp, w.k)
+        ref = oracle_final_ids(sp, red, w.kappa, w.k)
+        rec = {}
+        for st in stores:
+            b = idx[st]._buffers(nq, total, max(w.kappa, w.k), w.k)
+            _, fi = search_step(glv, idx[st], w, b, w.kappa)
+            got = fi.cpu().numpy()[qsel]
+            rec[st] = {"R1_vs_oracle_pipeline": recall_by_kind(got, ref, counts),
+                       "R2_vs_exact_top10": recall_by_kind(got, exact, counts)}
+        out["recall_10at10"] = rec
+        out["recall_sample"] = (f"{len(qsel)} queries ({', '.join(f'{n} {lab}' for lab, n in counts)}); oracle "
+                                f"restricted to the {len(sp['uniq'])} rows they touch")
+        if args.score_error and headline:
+            out["score_error_vs_fp64_oracle"] = score_error_block(glv, idx, w, sp, qsel, stores)
+        if name == "precision-10M-d128" or (headline and args.kappa_sweep not in ("auto", "none")):
+            kaps = KAPPA_SWEEP if args.kappa_sweep in ("auto",) else [int(x) for x in args.kappa_sweep.split(",")]
+            out["kappa_sweep"], out["equal_recall"] = kappa_sweep_block(glv, idx, w, stores, kaps, sp, red, exact,
+                                                                        qsel, counts, args, flush, world)
+        if headline and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_block(w, sp, qsel, args)
+    for ix in idx.values():
+        ix._buf = {}
+    del idx, w
+    torch.cuda.empty_cache()
+    return out
+
+
+def score_error_block(glv, idx, w, sp, qsel, stores):
+    """Reduced-space scores of the sample, each store against the unquantised FP64 oracle
+    (rows whose GPU tag differs from the oracle's near-tie decision are left out)."""
+    import numpy as np
+    import oracle as orc
+    nq = w.Q.shape[0]
+    offn = w.off.cpu().numpy()
+    red, _ = orc.score(orc.project(sp["Q"], sp["A"]), sp["Xr"], sp["tags"], sp["off"], sp["ids"])
+    gtags = next(iter(idx.values())).tags.cpu().numpy()
+    rows = sp["uniq"][sp["ids"]]
+    same = gtags[rows] == sp["tags"][sp["ids"]]
+    qn = np.linalg.norm(orc.project(sp["Q"], sp["A"]), axis=2)
+    xn = np.linalg.norm(sp["Xr"], axis=1)
+    cj = np.repeat(np.arange(len(qsel)), np.diff(sp["off"]))
+    scale = np.maximum(np.abs(red), qn[cj, sp["tags"][sp["ids"]]] * xn[sp["ids"]])
+    errs = {}
+    for st in stores:
+        ix = idx[st]
+        b = ix._buffers(nq, int(w.off[-1]), w.kappa, w.k)
+        glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"])
+        sc = glv.glv_score_candidates(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids)
+        allsc = sc.cpu().numpy()
+        got = np.concatenate([allsc[offn[j]:offn[j + 1]] for j in qsel])
+        rel = np.abs(got - red)[same] / scale[same]
+        errs[st] = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
+                    "p99_rel": float(np.quantile(rel, 0.99))}
+    return errs
+
+
+def kappa_sweep_block(glv, idx, w, stores, kaps, sp, red, exact, qsel, counts, args, flush, world):
+    """Each store at re-rank depths kappa in kaps: queries/s of the whole step and recall of the
+    final top 10 against the oracle pipeline at that kappa (R1) and against the exact top 10
+    (R2).  Equal recall: each store at the smallest kappa whose R2 reaches 0.9."""
+    nq = w.Q.shape[0]
+    sweep, best = {}, {}
+    for st in stores:
+        ix = idx[st]
+        rows = []
+        for kap in kaps:
+            if kap < w.k:
+                continue
+            r = time_search(glv, ix, w, kap, min(args.steps, 10), min(args.warmup, 2), flush, world)
+            b = ix._buffers(nq, int(w.off[-1]), kap, w.k)
+            _, fi = search_step(glv, ix, w, b, kap)
+            got = fi.cpu().numpy()[qsel]
+            rows.append({"kappa": kap, "value": r["value"], "ms_per_step": r["ms_per_step"],
+                         "kernels_ms": r["kernels_ms"],
+                         "R1": recall_by_kind(got, oracle_final_ids(sp, red, kap, w.k), counts)["all"],
+                         "R2": recall_by_kind(got, exact, counts)})
+        sweep[st] = rows
+        ok = [row for row in rows if row["R2"]["all"] >= 0.9]
+        best[st] = ({"kappa": ok[0]["kappa"], "value": ok[0]["value"], "R2": ok[0]["R2"]["all"]} if ok else
+                    {"kappa": None, "note": "no kappa of the sweep reaches R2 >= 0.9"})
+    return sweep, {"target": "R2 (final top 10 vs exact top 10 over the candidates) >= 0.9",
+                   "by_store": best}
+
+
+def cpu_baseline_block(w, sp, qsel, args):
+    """The FP64 oracle's whole search of a bounded sample of the queries, timed on the host
+    cores: all threads and one thread."""
+    import numpy as np
+    import oracle
+    nq = w.Q.shape[0]
+    if args.cpu_sample != len(qsel):
+        rng = np.random.default_rng(777)
+        csel = np.sort(rng.choice(nq, size=min(args.cpu_sample, nq), replace=False))
+        sp = oracle_subproblem(w, csel)
+    else:
+        csel = qsel
+    nthreads = os.cpu_count() or 1
+    oracle.set_threads(nthreads)
+    t_all, _, _ = oracle_search_timed(sp, w.kappa, w.k, repeats=3)
+    cores = oracle.get_threads()
+    n1 = max(1, len(csel) // 8)
+    sub = dict(sp)
+    sub["Q"] = sp["Q"][:n1]
+    sub["off"] = sp["off"][:n1 + 1]
+    sub["ids"] = sp["ids"][:int(sp["off"][n1])]
+    oracle.set_threads(1)
+    t_one, _, _ = oracle_search_timed(sub, w.kappa, w.k, repeats=1)
+    oracle.set_threads(nthreads)
+    return {"value": len(csel) / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(csel)} of the {nq} queries (all their candidates); reduced rows precomputed untimed "
+                      f"for the {len(sp['uniq'])} rows they touch; best of 3",
+            "single_thread": {"value": n1 / t_one, "unit": UNIT, "cores": 1,
+                              "sample": f"the first {n1} of those queries, one run"}}
+
+
+def run_glv(args):
     import torch
     import torch.distributed as dist
 
@@ -309,359 +887,78 @@ def run_glv(args):
 
     from paper_2410_22347_gb300 import build_lib
     build_lib.build()
-    from paper_2410_22347_gb300 import glv, synth
-    from paper_2410_22347_gb300.index import GleanVecIndex
+    from paper_2410_22347_gb300 import glv
 
-    w = synth.workload(args.workload, device=dev, replica=rank, queries=args.queries, **args.overrides)
-    nq, D = w.Q.shape
-    C, d, _ = w.A.shape
-    total = int(w.off[-1])
-    stores = [args.store] + [s for s in args.compare_stores.split(",") if s and s not in (args.store, "none")]
-    idx = {}
-    for st in stores:
-        idx[st] = GleanVecIndex(w.X, w.A, w.B, mu=w.mu if not idx else None,
-                                tags=None if not idx else next(iter(idx.values())).tags, store=st)
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    peaks["tf32_tflops"] = measure_tf32_peak(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
-
-    def step(ix, ev=None):
-        b = ix._buffers(nq, total, w.kappa, w.k)
-        if ev:
-            ev[0].record()
-        glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"], d_status=ix.status)
-        if ev:
-            ev[1].record()
-        glv.glv_score_topk(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids, w.kappa,
-                           scores_scratch=b["scores"], workspace=b["tws"], out_s=b["ts"], out_id=b["ti"], d_status=ix.status)
-        if ev:
-            ev[2].record()
-        glv.glv_rerank(w.X, w.Q, b["ti"], w.k, out_s=b["fs"], out_id=b["fi"], d_status=ix.status)
-        if ev:
-            ev[3].record()
-        return b["fs"], b["fi"]
-
-    # projection: 2 operand-prep launches + GEMM; (work plan +) fused score+top-k; re-rank
-    launches_per_step = 3 + 2
-    results = {}
-    tuned = {}
-    clocks = None
-    for si, st in enumerate(stores):
-        ix = idx[st]
-        if not args.no_autotune:  # untimed set-up: pick the scoring configuration for this store
-            from paper_2410_22347_gb300.autotune import tune_score
-            G, mode, carve, sched, table = tune_score(ix, w.Q, w.off, w.ids, w.kappa, use_cache=False)
-            tuned[st] = {"lanes_per_candidate": G, "gather_mode": mode, "smem_carveout_kb": carve,
-                         "schedule": sched, "ms_by_config(G/mode/carveout_kb/schedule)": table}
-        for _ in range(args.warmup):
-            step(ix)
-        torch.cuda.synchronize()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        sampler = ClockSampler(local) if si == 0 else None
-        if sampler:
-            sampler.__enter__()
-        t0 = time.perf_counter()
-        torch.cuda.nvtx.range_push(f"timed_{st}")  # lets a profiler select the timed launches
-        for s in range(args.steps):
-            flush.zero_()  # evict L2 between timed steps (not inside the timed events)
-            step(ix, evs[s])
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        if sampler:
-            sampler.__exit__()
-            clocks = sampler.summary()
-        if world > 1:
-            dist.barrier()
-        per_step = [evs[s][0].elapsed_time(evs[s][3]) for s in range(args.steps)]
-        kern = [[evs[s][t].elapsed_time(evs[s][t + 1]) for s in range(args.steps)] for t in range(3)]
-        tot_ms = max_over_ranks(sum(per_step))
-        assert ix.device_status() == 0, "device reported an error during the bench"
-        results[st] = dict(ms_per_step=tot_ms / args.steps,
-                           value=job_throughput(nq * args.steps, world, tot_ms),
-                           kernels_ms={n: statistics.mean(v) for n, v in
-                                       zip(("project", "score_topk", "rerank"), kern)},
-                           wall_s=wall)
-
-    # ---- batching: the step as one CUDA graph, and the per-query launch path ----
-    batching = {}
-    if args.graph or args.per_query:
-        ix = idx[args.store]
-        if args.graph:
-            g = torch.cuda.CUDAGraph()
-            side = torch.cuda.Stream()
-            side.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(side):
-                step(ix)  # warm the buffers on the capture stream
-            torch.cuda.current_stream().wait_stream(side)
-            torch.cuda.synchronize()
-            with torch.cuda.graph(g):
-                step(ix)
-            g.replay()
-            torch.cuda.synchronize()
-            gms = []
-            for _ in range(max(5, min(args.steps, 50))):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                g.replay()
-                e1.record()
-                e1.synchronize()
-                gms.append(e0.elapsed_time(e1))
-            gms_max = max_over_ranks(sum(gms) / len(gms))
-            batching["graph"] = {"ms_per_step": gms_max, "value": job_throughput(nq, world, gms_max)}
-        if args.per_query:
-            nsub = min(args.per_query, nq)
-            b = ix._buffers(nq, total, w.kappa, w.k)
-            fsz, isz = 4, 4
-            Qp1 = torch.empty(1, C, d, dtype=torch.float32, device=dev)
-            pws1 = torch.empty(max(glv.project_workspace_bytes(1, D, C, d, ix.compute), 1), dtype=torch.uint8,
-                               device=dev)
-            lib = glv.lib()
-            stv = glv._stream(None)
-
-            def one(j):
-                # every query on its own: projection, scoring + top-kappa, re-rank (pointer offsets)
-                lib.glv_project_queries(w.Q.data_ptr() + j * D * 4, 1, D, ix.A.data_ptr(), C, d, ix.compute,
-                                        Qp1.data_ptr(), pws1.data_ptr(), None, stv)
-                lib.glv_score_topk(Qp1.data_ptr(), 1, C, d, ix.Xred.data_ptr(), ix.row_stride,
-                                   None if ix.scales is None else ix.scales.data_ptr(), ix.dt, ix.tags.data_ptr(),
-                                   ix.N, w.off.data_ptr() + j * 8, w.ids.data_ptr(), total, w.kappa,
-                                   b["scores"].data_ptr(), b["tws"].data_ptr(), b["ts"].data_ptr() + j * w.kappa * fsz,
-                                   b["ti"].data_ptr() + j * w.kappa * isz, None, stv)
-                lib.glv_rerank(w.X.data_ptr(), ix.N, D, w.Q.data_ptr() + j * D * 4, 1,
-                               b["ti"].data_ptr() + j * w.kappa * isz, w.kappa, w.k,
-                               b["fs"].data_ptr() + j * w.k * fsz, b["fi"].data_ptr() + j * w.k * isz, None, stv)
-            for j in range(min(8, nsub)):
-                one(j)
-            torch.cuda.synchronize()
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for j in range(nsub):
-                one(j)
-            e1.record()
-            e1.synchronize()
-            pms = max_over_ranks(e0.elapsed_time(e1))
-            batching["per_query_launches"] = {"queries": nsub, "ms": pms,
-                                              "value": job_throughput(nsub, world, pms)}
-
-    # ---- lazy (Algorithm 3) vs eager (Algorithm 4) scoring + top-kappa ----
-    lazy = None
-    if args.lazy:
-        ix = idx[args.store]
-        b = ix._buffers(nq, total, w.kappa, w.k)
-        vis = torch.empty(nq, dtype=torch.int32, device=dev)
-
-        def lazy_step():
-            glv.glv_score_lazy(w.Q, ix.A, ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids,
-                               scores=b["scores"], visited=vis)
-            glv.glv_topk(b["scores"], w.off, w.ids, w.kappa, out_s=b["ts"], out_id=b["ti"])
-
-        def eager_step():
-            glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"])
-            glv.glv_score_topk(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off, w.ids, w.kappa,
-                               scores_scratch=b["scores"], workspace=b["tws"], out_s=b["ts"], out_id=b["ti"])
-
-        def timed(fn, reps=10):
-            fn()
-            torch.cuda.synchronize()
-            ms = []
-            for _ in range(reps):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                fn()
-                e1.record()
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            return sum(ms) / len(ms)
-        le, ee = timed(lazy_step), timed(eager_step)
-        v = vis.float()
-        lazy = {"lazy_ms": le, "eager_ms": ee, "visited_clusters_mean": float(v.mean()),
-                "visited_clusters_max": int(vis.max()), "clusters": C}
-
-    # ---- gather ceiling: the same rows for the same candidate ids, read with no arithmetic ----
-    ixc = idx[args.store]
-    gout = torch.empty(total, dtype=torch.float32, device=dev)
-    for _ in range(3):
-        glv.glv_gather_rows(ixc.Xred, ixc.row_stride, w.ids, out=gout)
-    torch.cuda.synchronize()
-    g_ms = []
-    for _ in range(10):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        glv.glv_gather_rows(ixc.Xred, ixc.row_stride, w.ids, out=gout)
-        e1.record()
-        e1.synchronize()
-        g_ms.append(e0.elapsed_time(e1))
-    gather_ms = sum(g_ms) / len(g_ms)
-    del gout
-
-
-    # Every step copies its queries and candidate lists from pinned host memory and reads
-    # its top-k back; steps stream through HostSearchPipeline, so step s+1's copies overlap
-    # step s's search.  The serial figure is one batch alone (copy in, search, copy out).
-    from paper_2410_22347_gb300.index import HostSearchPipeline
-    ix = idx[args.store]
-    Qh = w.Q.cpu().pin_memory()
-    offh = w.off.cpu().pin_memory()
-    idsh = w.ids.cpu().pin_memory()
-    outs = torch.empty(nq, w.k, dtype=torch.float32, pin_memory=True)
-    outi = torch.empty(nq, w.k, dtype=torch.int32, pin_memory=True)
-    for _ in range(max(1, args.warmup)):
-        ix.search_host(Qh, offh, idsh, w.kappa, w.k, outs, outi)
-    torch.cuda.synchronize()
-    e2e_steps = max(5, min(args.steps, 20))
-    e_ms = []
-    for _ in range(e2e_steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ix.search_host(Qh, offh, idsh, w.kappa, w.k, outs, outi)
-        e1.record()
-        e1.synchronize()
-        e_ms.append(e0.elapsed_time(e1))
-    serial_ms = max_over_ranks(sum(e_ms) / len(e_ms))
-    pipe = HostSearchPipeline(ix, w.kappa, w.k)
-    for _ in range(max(3, args.warmup)):
-        pipe.submit(Qh, offh, idsh, outs, outi)
-    pipe.synchronize()
-    pipe_steps = max(10, min(args.steps, 50))
-    flush.zero_()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    pipe.begin()
-    for _ in range(pipe_steps):
-        pipe.submit(Qh, offh, idsh, outs, outi)
-    e1.record()
-    e1.synchronize()
-    pipe.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / pipe_steps)
-    h2d = Qh.numel() * 4 + offh.numel() * 8 + idsh.numel() * 4
-    d2h = outs.numel() * 4 + outi.numel() * 4
-
-    # ---- recall vs the FP64 oracle (rank 0, bounded sample) and CPU baseline ----
-    line_extra = {}
-    if rank == 0:
-        import oracle
-        oracle.set_threads(os.cpu_count() or 1)
-        Xn = w.X.cpu().numpy()
-        Qn = w.Q.cpu().numpy()
-        mun, An, Bn = w.mu.cpu().numpy(), w.A.cpu().numpy(), w.B.cpu().numpy()
-        offn, idsn = w.off.cpu().numpy(), w.ids.cpu().numpy()
-        rng = np.random.default_rng(12345)
-        qsel = np.sort(rng.choice(nq, size=min(args.recall_sample, nq), replace=False))
-        sp = oracle_subproblem(Xn, Qn, mun, An, Bn, offn, idsn, qsel)
-        ot, os_, oid = oracle_search_timed(sp, w.kappa, w.k)
-        recall = {}
-        for st in stores:
-            fs, fi = step(idx[st])
-            torch.cuda.synchronize()
-            recall[st] = oracle.recall(fi.cpu().numpy()[qsel], oid)
-        line_extra["recall_10at10_vs_oracle"] = recall
-        if args.score_error:
-            # reduced-space scores of the sample, each store against the unquantised FP64 oracle
-            # (rows whose GPU tag differs from the oracle's near-tie decision are left out)
-            import oracle as orc
-            red, _ = orc.score(orc.project(sp["Q"], sp["A"]), sp["Xr"], sp["tags"], sp["off"], sp["ids"])
-            gtags = idx[args.store].tags.cpu().numpy()
-            rows = sp["uniq"][sp["ids"]]
-            same = gtags[rows] == sp["tags"][sp["ids"]]
-            qn = np.linalg.norm(orc.project(sp["Q"], sp["A"]), axis=2)
-            xn = np.linalg.norm(sp["Xr"], axis=1)
-            cj = np.repeat(np.arange(len(qsel)), np.diff(sp["off"]))
-            scale = np.maximum(np.abs(red), qn[cj, sp["tags"][sp["ids"]]] * xn[sp["ids"]])
-            errs = {}
-            for st in stores:
-                ix = idx[st]
-                b = ix._buffers(nq, total, w.kappa, w.k)
-                glv.glv_project_queries(w.Q, ix.A, ix.compute, Qp=b["Qp"], workspace=b["pws"])
-                sc = glv.glv_score_candidates(b["Qp"], ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, w.off,
-                                              w.ids)
-                allsc = sc.cpu().numpy()
-                got = np.concatenate([allsc[offn[j]:offn[j + 1]] for j in qsel])
-                rel = np.abs(got - red)[same] / scale[same]
-                errs[st] = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
-                            "p99_rel": float(np.quantile(rel, 0.99))}
-            line_extra["score_error_vs_fp64_oracle"] = errs
-        line_extra["recall_sample"] = f"{len(qsel)} random queries; oracle restricted to the rows they touch"
-        if not args.no_cpu_baseline:
-            csel = qsel if args.cpu_sample == len(qsel) else np.sort(
-                rng.choice(nq, size=min(args.cpu_sample, nq), replace=False))
-            cp = sp if csel is qsel else oracle_subproblem(Xn, Qn, mun, An, Bn, offn, idsn, csel)
-            ctime, _, _ = oracle_search_timed(cp, w.kappa, w.k, repeats=3)
-            line_extra["cpu_baseline"] = {
-                "value": len(csel) / ctime, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-                "sample": f"{len(csel)} of the {nq} queries (all {w.ids.shape[0] // nq} candidates each); "
-                          f"reduced rows precomputed untimed for the {len(cp['uniq'])} rows they touch; best of 3"}
-
+    head_store, others = STORES.get(args.workload, ("bf16", ""))
+    store = args.store or head_store
+    compare = others if args.compare_stores is None else args.compare_stores
+    stores = [store] + [s for s in compare.split(",") if s and s not in (store, "none")]
+    common = dict(dev=dev, rank=rank, world=world, local=local, flush=flush, peaks=peaks)
+    head = measure_workload(args.workload, args, stores=stores, headline=True, overrides=args.overrides, **common)
+    configs = {}
+    if args.configs == "auto":
+        extra = EXTRA_CONFIGS if (args.workload == HEADLINE and not args.overrides) else ()
+    else:
+        extra = tuple(c for c in args.configs.split(",") if c and c != "none")
+    for name in extra:
+        hs, ot = STORES[name]
+        st = [hs] + [s for s in ot.split(",") if s]
+        cfg = measure_workload(name, args, stores=st, headline=False, overrides={}, **common)
+        cfg.pop("_results")
+        cfg.pop("_launches_per_step")
+        configs[name] = cfg
     if world > 1:
         dist.barrier()
     if rank != 0:
         return 0
 
-    head = results[args.store]
-    hbm, peak_kind = measured_peaks()
-    eb = glv.elem_bytes(glv.DTYPES[args.store])
-    bytes_per_cand = d * eb + (4 if args.store == "fp8" else 0) + 4
-    alg_bytes = total * bytes_per_cand
-    score_ms = head["kernels_ms"]["score_topk"]
-    achieved = alg_bytes / (score_ms / 1e3) / 1e9
-    traffic = recorded_traffic(args.workload, args.store)
-    rec = line_extra.get("recall_10at10_vs_oracle", {}).get(args.store)
+    res = head.pop("_results")
+    lps = head.pop("_launches_per_step")
+    hs = head["stores"][store]
+    rec = head.get("recall_10at10", {}).get(store, {}).get("R1_vs_oracle_pipeline", {}).get("all")
+    idx_compute = head["projection"].get(store, {}).get("operands", "")
     line = {
         "metric": METRIC,
-        "value": head["value"],
+        "value": hs["value"],
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": head["ms_per_step"],
+        "ms_per_step": hs["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": args.store,
+        "dtype": store,
         "data": "synthetic",
-        "config": {"workload": args.workload, "overrides": args.overrides or None, "N": int(w.X.shape[0]), "D": D, "d": d, "C": C,
-                   "queries_per_gpu": nq, "candidates_per_query": total // nq, "kappa": w.kappa, "k": w.k,
-                   "reduced_row_store": args.store, "accumulate": "f32",
-                   "projection": {0: "f32 (tcgen05 3xTF32)", 1: "bf16 (tcgen05)"}[idx[args.store].compute],
+        "config": {"workload": args.workload, "overrides": args.overrides or None, "N": head["N"], "D": head["D"],
+                   "d": head["d"], "C": head["C"], "queries_per_gpu": head["queries"],
+                   "candidates_per_query": head["candidates_per_query"], "kappa": head["kappa"], "k": head["k"],
+                   "reduced_row_store": store, "accumulate": "f32", "projection_operands": idx_compute,
+                   "query_mix": head["query_mix"],
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "glv_score_topk (score_topk_kernel)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs",
-                     "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
-                     "bytes_per_candidate": bytes_per_cand, "kernel_ms": score_ms,
-                     "gather_ceiling": {
-                         "kernel": "glv_gather_rows (same rows, same ids, no arithmetic)",
-                         "ms": gather_ms,
-                         "achieved_GBs": total * (ixc.row_stride + 8) / (gather_ms / 1e3) / 1e9,
-                         "frac_of_copy_peak": total * (ixc.row_stride + 8) / (gather_ms / 1e3) / 1e9 / hbm,
-                         "score_topk_frac_of_ceiling": gather_ms / score_ms}},
-        "kernels_ms": head["kernels_ms"],
-        "e2e": {"value": job_throughput(nq, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                "path": f"HostSearchPipeline, {pipe_steps} steps streamed (copies of step s+1 overlap the "
-                        f"search of step s); inputs larger than L2 (reduced store + re-rank rows)",
-                "serial_ms_per_batch": serial_ms},
-        "gpu_launches": (launches_per_step + (1 if (tuned.get(args.store) or {}).get("schedule", 1) == 1 else 0))
-                        * args.steps,
-        "clocks": clocks,
-        "modes": {st: {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernels_ms": r["kernels_ms"]}
-                  for st, r in results.items()},
-        "autotune": tuned or None,
-        "batching": batching or None,
-        "lazy_vs_eager": lazy,
+        "roofline": hs["roofline"],
+        "kernels_ms": hs["kernels_ms"],
+        "e2e": head.get("e2e"),
+        "gpu_launches": lps[store] * args.steps,
+        "clocks": head["clocks"],
+        "modes": head["stores"],
+        "autotune": head["autotune"],
+        "build": head["build"],
+        "projection": head["projection"],
+        "peaks": {k: v for k, v in peaks.items()},
+        "recall_10at10": head.get("recall_10at10"),
+        "recall_sample": head.get("recall_sample"),
+        "cpu_baseline": head.get("cpu_baseline"),
+        "configs": configs or None,
     }
-    line.update(line_extra)
+    for k in ("batching", "lazy_vs_eager", "score_error_vs_fp64_oracle", "kappa_sweep", "equal_recall"):
+        if k in head:
+            line[k] = head[k]
     if rec is not None and rec < 0.9:
-        line["warning"] = f"{args.store} recall {rec:.3f} below 0.9"
+        line["warning"] = f"{store} recall {rec:.3f} below 0.9"
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -671,8 +968,9 @@ def run_glv(args):
 def run_learn(args):
     """Differentiation workload: 200k database + 20k OOD learning queries, D = 768, d = 128,
     C = 16.  Times the FP64 second moments, the LeanVec-Sphering initialisation (host
-    eigendecompositions) and refinement minibatches of 4096 pairs (forward + backward +
-    Adam), and checks one minibatch gradient against the FP64 oracle."""
+    Cholesky and eigendecompositions) and refinement minibatches of 4096 pairs (forward,
+    loss, backward and Adam, all in the library's kernels), and checks one minibatch gradient
+    against the FP64 oracle."""
     import numpy as np
     import torch
     from paper_2410_22347_gb300 import build_lib
@@ -711,15 +1009,20 @@ def run_learn(args):
     P = 4096
     A = A0.clone().requires_grad_(True)
     B = B0.clone().requires_grad_(True)
-    opt = torch.optim.Adam([A, B], lr=1e-4)
+    adam = [(torch.zeros_like(A), torch.zeros_like(A)), (torch.zeros_like(B), torch.zeros_like(B))]
+    nstep = [0]
 
     def minibatch():
         qi = torch.randint(0, w.Q.shape[0], (P,), generator=g, device=dev, dtype=torch.int32)
         xi = torch.randint(0, n, (P,), generator=g, device=dev, dtype=torch.int32)
-        opt.zero_grad(set_to_none=True)
+        A.grad = None
+        B.grad = None
         loss = learn.pair_loss(A, B, w.Q, w.X, tags, qi, xi)
         loss.backward()
-        opt.step()
+        nstep[0] += 1
+        with torch.no_grad():
+            for prm, (m, v) in zip((A, B), adam):
+                learn.glv_adam_step(prm, prm.grad, m, v, nstep[0], 1e-4)
         return loss
     for _ in range(args.warmup):
         minibatch()
@@ -737,7 +1040,8 @@ def run_learn(args):
     xi = torch.randint(0, n, (P,), generator=g, device=dev, dtype=torch.int32)
     Ad, Bd = A.detach(), B.detach()
     s, t, u, v = learn.glv_pair_forward(w.Q, w.X, tags, Ad, Bd, qi, xi)
-    dA, dB = learn.glv_pair_backward(w.Q, w.X, tags, C, qi, xi, u, v, -2.0 * (t - s))
+    _, gp = learn.glv_pair_loss(s, t, want_loss=False, want_grad=True)
+    dA, dB = learn.glv_pair_backward(w.Q, w.X, tags, C, qi, xi, u, v, gp)
     qn, xn = qi.cpu().numpy(), xi.cpu().numpy()
     sub_q, sub_x = np.unique(qn), np.unique(xn)
     Qs, Xs = w.Q.cpu().numpy()[sub_q], w.X.cpu().numpy()[sub_x]

@@ -141,7 +141,9 @@ glv_status glv_build_reduced(const float* X, int64_t N, int32_t D, const uint16_
  *           GLV_ERR_UNSUPPORTED and enqueue nothing (use glv_build_reduced instead).
  *   Set-up: the first call on each device looks up the array's device address with that
  *           device current (cudaGetSymbolAddress) and caches it; make that first call before
- *           any stream capture on that device.
+ *           any stream capture on that device.  The cached address belongs to the device's
+ *           context of that first call: after cudaDeviceReset() on a device, do not call this
+ *           entry point on that device again in the same process.
  *   Sharing: all calls on a device share the one array and it keeps the previous call's
  *           contents (the parts that must start at zero are cleared on the stream by each
  *           call).  Calls whose execution overlaps on the GPU -- on different streams, or
@@ -277,7 +279,8 @@ glv_status glv_get_score_config(glv_dtype dt, int32_t d, int32_t* lanes_per_cand
  * results and errors as those calls, in that order; the intermediate arrays (projected
  * queries, projection operands, score scratch, work plan, survivors) are carved from one
  * caller-provided workspace of glv_search_workspace_size(nq, D, C, d, compute,
- * n_candidates, kappa) bytes, 256-byte aligned, contents on entry irrelevant.
+ * n_candidates, kappa) bytes, 256-byte aligned, contents on entry irrelevant.  The arguments
+ * of all three steps are checked before the first launch is enqueued.
  *   X : N x D float32 (the re-rank's rows);  Q : nq x D float32;  A : C x d x D float32.
  *   compute : projection operands, GLV_F32 (3xTF32, FP32-accurate) or GLV_BF16.
  *   Xred, row_stride, scales, dt, tags, cand_off, cand_ids, n_candidates : as for
@@ -291,6 +294,32 @@ glv_status glv_search(const float* X, int64_t N, int32_t D, const float* Q, int6
                       const int64_t* cand_off, const int32_t* cand_ids, int64_t n_candidates,
                       int32_t kappa, int32_t k, void* workspace, float* out_s, int32_t* out_id,
                       int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * The same search from HOST buffers (the serving entry point): copies the queries and the
+ * candidate lists from host memory into the workspace, runs glv_search on them and copies
+ * the top k back to host memory, all enqueued on `stream` in that order (cudaMemcpyAsync;
+ * the call returns after enqueueing).  Host buffers should be page-locked (cudaHostAlloc /
+ * cudaHostRegister) for the copies to be asynchronous; with pageable memory they still
+ * complete correctly but may synchronise the host.  The caller must not touch the host
+ * outputs, nor reuse the host inputs or the workspace, until the stream has passed this
+ * call.  Two calls on two streams with two workspaces overlap one batch's copies with the
+ * other's search.
+ *   Q_host : nq x D float32;  cand_off_host : nq + 1 int64;  cand_ids_host : n_candidates
+ *   int32 (host);  out_s_host, out_id_host : nq x k (host).   X, A, Xred, scales, tags, as
+ *   for glv_search, are device pointers.
+ *   workspace : glv_search_host_workspace_size(nq, D, C, d, compute, n_candidates, kappa, k)
+ *   bytes of device memory, 256-byte aligned.
+ * Every argument of every step is checked before the first copy is enqueued.
+ * ------------------------------------------------------------------------------------- */
+size_t glv_search_host_workspace_size(int64_t nq, int32_t D, int32_t C, int32_t d, glv_dtype compute,
+                                      int64_t n_candidates, int32_t kappa, int32_t k);
+glv_status glv_search_host(const float* X, int64_t N, int32_t D, const float* Q_host, int64_t nq,
+                           const float* A, int32_t C, int32_t d, glv_dtype compute, const void* Xred,
+                           int64_t row_stride, const float* scales, glv_dtype dt, const uint16_t* tags,
+                           const int64_t* cand_off_host, const int32_t* cand_ids_host, int64_t n_candidates,
+                           int32_t kappa, int32_t k, void* workspace, float* out_s_host, int32_t* out_id_host,
+                           int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Gather calibration (no counterpart in the paper; a measuring instrument for the roofline
@@ -379,6 +408,30 @@ glv_status glv_pair_backward(const float* Q, int64_t nQ, const float* X, int64_t
                              const int32_t* xi, int64_t P, const float* u, const float* v,
                              const float* g, float* dA, float* dB, void* workspace,
                              int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Pair loss, the inner-product approximation loss of Section 2.1 over GleanVec pairs:
+ *     loss = sum_p (t_p - s_p)^2       (FP64 accumulation, deterministic order),
+ *     g_p  = w * dloss/ds_p = -2 w (t_p - s_p)      (FP32),
+ * from the s, t of glv_pair_forward.  weight: device pointer to one double w (the upstream
+ * derivative of an outer objective with respect to loss), or NULL for w = 1.  loss: device
+ * pointer to one double (8-byte aligned), or NULL;  g: P float32, or NULL (not both NULL).
+ * One CTA; meant for minibatches (thousands of pairs).
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_pair_loss(const float* s, const float* t, int64_t P, const double* weight, double* loss, float* g,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * One Adam step (Kingma and Ba, 2015) on n FP32 parameters, in place -- the optimiser that
+ * refines the Sphering initialisation with the gradients of glv_pair_backward (the paper
+ * fixes no optimiser; it has no counterpart there):
+ *     m <- beta1 m + (1 - beta1) grad,   v <- beta2 v + (1 - beta2) grad^2,
+ *     param <- param - lr * (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps).
+ *   param, m, v : n float32, updated (m, v start at zero before step 1).   grad : n float32.
+ *   step : 1-based step count.  0 <= beta1, beta2 < 1, eps > 0, lr >= 0.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_adam_step(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                         float beta2, float eps, int32_t step, void* stream);
 
 #ifdef __cplusplus
 }

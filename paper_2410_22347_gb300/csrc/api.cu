@@ -68,8 +68,19 @@ static glv_status fill_score_args(ScoreArgs& a, const float* Qp, int64_t nq, int
 
 }  // namespace
 
+// While a composite call (glv_search, glv_search_host) validates the calls it is made of, the
+// entry points run their argument checks and return before their first launch: every check
+// of every step passes before anything is enqueued.
+static thread_local bool g_checks_only = false;
+
+struct ChecksOnly {
+  ChecksOnly() { g_checks_only = true; }
+  ~ChecksOnly() { g_checks_only = false; }
+};
+
 #define GLV_LAUNCH(expr)                            \
   do {                                              \
+    if (g_checks_only) return GLV_OK;               \
     cudaError_t _e = (expr);                        \
     if (_e != cudaSuccess) return GLV_ERR_CUDA;     \
   } while (0)
@@ -331,6 +342,27 @@ glv_status glv_pair_backward(const float* Q, int64_t nQ, const float* X, int64_t
   return GLV_OK;
 }
 
+glv_status glv_pair_loss(const float* s, const float* t, int64_t P, const double* weight, double* loss, float* g,
+                         void* stream) {
+  GLV_CHECK(P >= 0, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(loss || g, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(P == 0 || (s && t), GLV_ERR_INVALID_ARG);
+  GLV_CHECK(aligned(loss, 8), GLV_ERR_INVALID_ARG);
+  GLV_LAUNCH(launch_pair_loss(s, t, P, weight, loss, g, (cudaStream_t)stream));
+  return GLV_OK;
+}
+
+glv_status glv_adam_step(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                         float beta2, float eps, int32_t step, void* stream) {
+  GLV_CHECK(n >= 0 && step >= 1, GLV_ERR_INVALID_ARG);
+  GLV_CHECK(lr >= 0.f && beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f,
+            GLV_ERR_INVALID_ARG);
+  if (n == 0) return GLV_OK;
+  GLV_CHECK(param && grad && m && v, GLV_ERR_INVALID_ARG);
+  GLV_LAUNCH(launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, num_sms(), (cudaStream_t)stream));
+  return GLV_OK;
+}
+
 size_t glv_kmeans_workspace_size(int64_t N, int32_t D, int32_t C) {
   if (N < 0 || D < 1 || C < 1) return 0;
   return kmeans_ws_bytes(N, C, D);
@@ -372,11 +404,84 @@ size_t glv_search_workspace_size(int64_t nq, int32_t D, int32_t C, int32_t d, gl
   return b;
 }
 
+static glv_status search_steps(const float* X, int64_t N, int32_t D, const float* Q, int64_t nq, const float* A,
+                               int32_t C, int32_t d, glv_dtype compute, const void* Xred, int64_t row_stride,
+                               const float* scales, glv_dtype dt, const uint16_t* tags, const int64_t* cand_off,
+                               const int32_t* cand_ids, int64_t n_candidates, int32_t kappa, int32_t k,
+                               void* workspace, float* out_s, int32_t* out_id, int32_t* d_status, void* stream);
+
 glv_status glv_search(const float* X, int64_t N, int32_t D, const float* Q, int64_t nq, const float* A,
                       int32_t C, int32_t d, glv_dtype compute, const void* Xred, int64_t row_stride,
                       const float* scales, glv_dtype dt, const uint16_t* tags, const int64_t* cand_off,
                       const int32_t* cand_ids, int64_t n_candidates, int32_t kappa, int32_t k, void* workspace,
                       float* out_s, int32_t* out_id, int32_t* d_status, void* stream) {
+  {
+    ChecksOnly guard;
+    const glv_status st = search_steps(X, N, D, Q, nq, A, C, d, compute, Xred, row_stride, scales, dt, tags,
+                                       cand_off, cand_ids, n_candidates, kappa, k, workspace, out_s, out_id,
+                                       d_status, stream);
+    if (st != GLV_OK) return st;
+  }
+  return search_steps(X, N, D, Q, nq, A, C, d, compute, Xred, row_stride, scales, dt, tags, cand_off, cand_ids,
+                      n_candidates, kappa, k, workspace, out_s, out_id, d_status, stream);
+}
+
+size_t glv_search_host_workspace_size(int64_t nq, int32_t D, int32_t C, int32_t d, glv_dtype compute,
+                                      int64_t n_candidates, int32_t kappa, int32_t k) {
+  if (nq < 0 || D < 1 || k < 1 || n_candidates < 0) return 0;
+  size_t b = round_up256((size_t)nq * D * sizeof(float));                              // queries
+  b += round_up256((size_t)(nq + 1) * sizeof(int64_t));                                // list offsets
+  b += round_up256((size_t)(n_candidates > 0 ? n_candidates : 1) * sizeof(int32_t));  // candidate ids
+  b += round_up256((size_t)nq * k * 8);                                                // top k
+  return b + glv_search_workspace_size(nq, D, C, d, compute, n_candidates, kappa);
+}
+
+glv_status glv_search_host(const float* X, int64_t N, int32_t D, const float* Q_host, int64_t nq,
+                           const float* A, int32_t C, int32_t d, glv_dtype compute, const void* Xred,
+                           int64_t row_stride, const float* scales, glv_dtype dt, const uint16_t* tags,
+                           const int64_t* cand_off_host, const int32_t* cand_ids_host, int64_t n_candidates,
+                           int32_t kappa, int32_t k, void* workspace, float* out_s_host, int32_t* out_id_host,
+                           int32_t* d_status, void* stream) {
+  GLV_CHECK(nq >= 0 && D >= 1 && k >= 1 && n_candidates >= 0, GLV_ERR_INVALID_ARG);
+  if (nq == 0) return GLV_OK;
+  GLV_CHECK(Q_host && cand_off_host && out_s_host && out_id_host && (cand_ids_host || n_candidates == 0),
+            GLV_ERR_INVALID_ARG);
+  GLV_CHECK(workspace && aligned(workspace, 256), GLV_ERR_INVALID_ARG);
+  uint8_t* w = static_cast<uint8_t*>(workspace);
+  float* Qd = reinterpret_cast<float*>(w);
+  w += round_up256((size_t)nq * D * sizeof(float));
+  int64_t* offd = reinterpret_cast<int64_t*>(w);
+  w += round_up256((size_t)(nq + 1) * sizeof(int64_t));
+  int32_t* idsd = reinterpret_cast<int32_t*>(w);
+  w += round_up256((size_t)(n_candidates > 0 ? n_candidates : 1) * sizeof(int32_t));
+  float* sd = reinterpret_cast<float*>(w);
+  int32_t* idd = reinterpret_cast<int32_t*>(w + (size_t)nq * k * sizeof(float));
+  w += round_up256((size_t)nq * k * 8);
+  {
+    ChecksOnly guard;
+    const glv_status st = search_steps(X, N, D, Qd, nq, A, C, d, compute, Xred, row_stride, scales, dt, tags, offd,
+                                       idsd, n_candidates, kappa, k, w, sd, idd, d_status, stream);
+    if (st != GLV_OK) return st;
+  }
+  const cudaStream_t cs = (cudaStream_t)stream;
+  GLV_LAUNCH(cudaMemcpyAsync(Qd, Q_host, (size_t)nq * D * sizeof(float), cudaMemcpyHostToDevice, cs));
+  GLV_LAUNCH(cudaMemcpyAsync(offd, cand_off_host, (size_t)(nq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, cs));
+  if (n_candidates > 0)
+    GLV_LAUNCH(cudaMemcpyAsync(idsd, cand_ids_host, (size_t)n_candidates * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, cs));
+  const glv_status st = search_steps(X, N, D, Qd, nq, A, C, d, compute, Xred, row_stride, scales, dt, tags, offd,
+                                     idsd, n_candidates, kappa, k, w, sd, idd, d_status, stream);
+  if (st != GLV_OK) return st;
+  GLV_LAUNCH(cudaMemcpyAsync(out_s_host, sd, (size_t)nq * k * sizeof(float), cudaMemcpyDeviceToHost, cs));
+  GLV_LAUNCH(cudaMemcpyAsync(out_id_host, idd, (size_t)nq * k * sizeof(int32_t), cudaMemcpyDeviceToHost, cs));
+  return GLV_OK;
+}
+
+static glv_status search_steps(const float* X, int64_t N, int32_t D, const float* Q, int64_t nq, const float* A,
+                               int32_t C, int32_t d, glv_dtype compute, const void* Xred, int64_t row_stride,
+                               const float* scales, glv_dtype dt, const uint16_t* tags, const int64_t* cand_off,
+                               const int32_t* cand_ids, int64_t n_candidates, int32_t kappa, int32_t k,
+                               void* workspace, float* out_s, int32_t* out_id, int32_t* d_status, void* stream) {
   GLV_CHECK(nq >= 0 && k >= 1 && kappa >= 0 && (kappa == 0 || kappa >= k), GLV_ERR_INVALID_ARG);
   GLV_CHECK(k <= GLV_MAX_KAPPA && kappa <= GLV_MAX_KAPPA && n_candidates >= 0, GLV_ERR_INVALID_ARG);
   GLV_CHECK(compute == GLV_F32 || compute == GLV_BF16, GLV_ERR_INVALID_ARG);

@@ -127,6 +127,10 @@ cudaError_t launch_pair_backward(const float* Q, int64_t nQ, const float* X, int
                                  const uint16_t* tags, int C, int d, const int32_t* qi, const int32_t* xi, int64_t P,
                                  const float* u, const float* v, const float* g, float* dA, float* dB, void* ws,
                                  int32_t* d_status, cudaStream_t st);
+cudaError_t launch_pair_loss(const float* s, const float* t, int64_t P, const double* weight, double* loss, float* g,
+                             cudaStream_t st);
+cudaError_t launch_adam(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                        float eps, int step, int num_sms, cudaStream_t st);
 cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags, const float* B,
                          int C, int d, int dt, void* Xred, int64_t row_stride, float* scales,
                          void* workspace, int32_t* d_status, cudaStream_t st);

@@ -372,4 +372,72 @@ cudaError_t launch_pair_backward(const float* Q, int64_t nQ, const float* X, int
   return cudaGetLastError();
 }
 
+// ---- pairs: loss and its gradient with respect to s -----------------------------------------
+//
+// L = sum_p (t_p - s_p)^2, the inner-product approximation loss of Section 2.1 over the pairs,
+// and g_p = dL/ds_p = -2 (t_p - s_p), scaled by an upstream weight w (dOut/dL; 1 if absent).
+// One CTA, a fixed assignment of pairs to threads and a fixed reduction tree: the FP64 loss is
+// the same on every call for the same inputs.
+
+constexpr int kLossThreads = 1024;
+
+__global__ void __launch_bounds__(kLossThreads) pair_loss_kernel(const float* __restrict__ s,
+                                                               const float* __restrict__ t, int64_t P,
+                                                               const double* __restrict__ weight,
+                                                               double* __restrict__ loss, float* __restrict__ g) {
+  __shared__ double part[kLossThreads / 32];
+  const float w = weight ? (float)*weight : 1.f;
+  double acc = 0.0;
+  for (int64_t p = threadIdx.x; p < P; p += kLossThreads) {
+    const float r = t[p] - s[p];
+    if (g) g[p] = -2.f * w * r;
+    acc = fma((double)r, (double)r, acc);
+  }
+  if (!loss) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = part[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) *loss = v;
+  }
+}
+
+cudaError_t launch_pair_loss(const float* s, const float* t, int64_t P, const double* weight, double* loss, float* g,
+                             cudaStream_t st) {
+  pair_loss_kernel<<<1, kLossThreads, 0, st>>>(s, t, P, weight, loss, g);
+  return cudaGetLastError();
+}
+
+// ---- Adam (Kingma & Ba, 2015) ------------------------------------------------------------------
+//
+// m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+// param <- param - lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+// The bias corrections are formed on the host in double and passed in.
+
+__global__ void adam_kernel(float* __restrict__ param, const float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    param[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+cudaError_t launch_adam(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                        float eps, int step, int num_sms, cudaStream_t st) {
+  const double c1 = 1.0 - pow((double)b1, (double)step), c2 = 1.0 - pow((double)b2, (double)step);
+  const int64_t want = (n + 255) / 256;
+  const int blocks = (int)(want < (int64_t)num_sms * 8 ? (want > 0 ? want : 1) : (int64_t)num_sms * 8);
+  adam_kernel<<<blocks, 256, 0, st>>>(param, grad, m, v, n, lr, b1, b2, eps, (float)c1, (float)c2);
+  return cudaGetLastError();
+}
+
 }  // namespace glv

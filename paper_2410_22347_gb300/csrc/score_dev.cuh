@@ -147,6 +147,35 @@ GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
   }
 }
 
+// 16-byte asynchronous copy global -> shared that bypasses L1 (cp.async.cg); src_bytes < 16
+// fills the rest of the 16 bytes with zeros.  Completes at cp_async_wait_all.
+GLV_DEV void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+
+// Whether stage_qp_async can stage this problem's projected views (the float4 layout).
+GLV_DEV bool qp_async_ok(const ScoreArgs& a) {
+  return (a.d & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Qp) & 15) == 0;
+}
+
+// stage_qp's float4 path as asynchronous copies: every float4 of the query's C projected views
+// (and the zero padding up to dpad) goes straight from global memory to its slot of the
+// sub-block layout, without passing through registers; the copies complete at
+// cp_async_wait_all.  Needs qp_async_ok(a).
+template <int DT>
+GLV_DEV void stage_qp_async(const ScoreArgs& a, int64_t j, float* qs) {
+  constexpr int EPC = Elem<DT>::kPerChunk;
+  const float* qj = a.Qp + j * (int64_t)a.C * a.d;
+  const int q4 = (a.nch * EPC) >> 2, total4 = a.C * q4;
+  for (int t = threadIdx.x; t < total4; t += blockDim.x) {
+    const int c = t / q4, r = (t - c * q4) * 4;
+    const int ch = r / EPC, e = r - ch * EPC;
+    const bool in = r < a.d;
+    cp_async16(qs + c * a.qstride + ((e >> 2) * a.sbs + ch) * 4, in ? qj + (int64_t)c * a.d + r : qj, in ? 16 : 0);
+  }
+}
+
 // Score candidates p in [b0, b1) with the CTA's warps; sink(p, score) receives each score
 // (from lane 0 of the candidate's lane group).  A bad id or tag scores -inf and is reported.
 // PIPE: the row loads of the next candidate are issued before the current one is computed

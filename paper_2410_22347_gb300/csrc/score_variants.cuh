@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
       }
     }
     const int64_t j = s_rec[cur].q;
-    if (j != s_staged) stage_qp<DT>(a, j, qs);
+    if (j != s_staged) stage_qp<DT>(a, j, qs);  // else its views were copied during the last selection
+    cp_async_wait_all();
     __syncthreads();
     if (threadIdx.x == 0) s_staged = j;
     const int64_t b0 = s_rec[cur].b0, b1 = b0 + s_rec[cur].len;
@@ -188,8 +189,9 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
     }
     if (threadIdx.x == 0) cp_async_wait_all();
     __syncthreads();
-    // while this item is being selected, let DRAM fetch the start of the next one: its first
-    // rows (one per thread) and its query's projected views go to L2
+    // while this item is being selected (the selection does not read qs), the next item's
+    // query views are copied into qs asynchronously, and DRAM fetches the next item's first
+    // rows (one per thread) into L2
     if (s_valid[cur ^ 1]) {
       const int64_t nb0 = s_rec[cur ^ 1].b0, nq = s_rec[cur ^ 1].q;
       const int nlen = s_rec[cur ^ 1].len;
@@ -198,7 +200,10 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
         if (id >= 0 && id < a.N) prefetch_l2_bulk(a.Xred + id * a.row_stride, (uint32_t)a.row_stride);
       }
       const int64_t qbytes = (int64_t)a.C * a.d * 4;
-      if (nq != s_staged && (qbytes & 15) == 0) {
+      if (nq != j && qp_async_ok(a)) {
+        stage_qp_async<DT>(a, nq, qs);
+        if (threadIdx.x == 0) s_staged = nq;  // read again only after the selection's barriers
+      } else if (nq != j && (qbytes & 15) == 0) {
         const int pieces = (int)((qbytes + 4095) / 4096);
         const int t = (int)blockDim.x - 1 - (int)threadIdx.x;
         if (t < pieces) {

@@ -60,6 +60,9 @@ def _load() -> ctypes.CDLL:
         "glv_search_workspace_size": (sz, [i64, i32, i32, i32, i32, i64, i32]),
         "glv_search": (i32, [P, i64, i32, P, i64, P, i32, i32, i32, P, i64, P, i32, P, P, P, i64, i32, i32,
                              P, P, P, P, P]),
+        "glv_search_host_workspace_size": (sz, [i64, i32, i32, i32, i32, i64, i32, i32]),
+        "glv_search_host": (i32, [P, i64, i32, P, i64, P, i32, i32, i32, P, i64, P, i32, P, P, P, i64, i32, i32,
+                                  P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -381,3 +384,40 @@ def glv_search(X, Q, A, compute: int, Xred, row_stride: int, scales, dt: int, ta
                                          _ptr(workspace), _ptr(out_s), _ptr(out_id), _ptr(d_status),
                                          _stream(stream)))
     return out_s, out_id
+
+
+def search_host_workspace_bytes(nq: int, D: int, C: int, d: int, compute: int, n_candidates: int, kappa: int,
+                                k: int) -> int:
+    return int(_lib.glv_search_host_workspace_size(nq, D, C, d, compute, n_candidates, kappa, k))
+
+
+def _need_host(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def glv_search_host(X, Q_h, A, compute: int, Xred, row_stride: int, scales, dt: int, tags, off_h, ids_h, kappa: int,
+                    k: int, workspace, out_s_h, out_id_h, d_status=None, stream=None):
+    """glv_search from host buffers: Q_h, off_h, ids_h in and out_s_h, out_id_h out are host tensors
+    (pinned for asynchronous copies); the copies and the search are enqueued on ``stream``."""
+    _need(X, torch.float32, "X", 2)
+    _need(A, torch.float32, "A", 3)
+    _need(tags, torch.uint16, "tags", 1)
+    _need_host(Q_h, torch.float32, "Q_h")
+    _need_host(off_h, torch.int64, "off_h")
+    _need_host(ids_h, torch.int32, "ids_h")
+    _need_host(out_s_h, torch.float32, "out_s_h")
+    _need_host(out_id_h, torch.int32, "out_id_h")
+    N, D = X.shape
+    nq = Q_h.shape[0]
+    C, d, _ = A.shape
+    _check("glv_search_host", _lib.glv_search_host(
+        _ptr(X), N, D, ctypes.c_void_p(Q_h.data_ptr()), nq, _ptr(A), C, d, compute, _ptr(Xred), row_stride,
+        _ptr(scales), dt, _ptr(tags), ctypes.c_void_p(off_h.data_ptr()), ctypes.c_void_p(ids_h.data_ptr()),
+        ids_h.shape[0], kappa, k, _ptr(workspace), ctypes.c_void_p(out_s_h.data_ptr()),
+        ctypes.c_void_p(out_id_h.data_ptr()), _ptr(d_status), _stream(stream)))
+    return out_s_h, out_id_h

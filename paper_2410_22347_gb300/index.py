@@ -7,9 +7,10 @@ search of Algorithm 1 / Algorithm 4 with four library calls:
     glv_project_queries -> glv_score_topk (fused scoring + top-kappa) -> glv_rerank
 
 ``search`` takes device tensors; ``search_host`` takes host tensors (pinned when given
-pinned memory), copies them in, searches and copies the top-k back on the same stream.
-``HostSearchPipeline`` streams a sequence of host-resident batches: the copies of the next
-batch run on a copy stream while the current one is searched.  Every step runs in libglv's
+pinned memory) and runs the library's host-buffer entry point, which copies them in, searches
+and copies the top-k back on one stream.  ``HostSearchPipeline`` streams a sequence of
+host-resident batches over alternating streams, so one batch's copies overlap another's
+search.  Every step runs in libglv's
 kernels; torch only provides device memory and the streams.
 """
 from __future__ import annotations
@@ -82,30 +83,29 @@ class GleanVecIndex:
 
     def search_host(self, Q_h: torch.Tensor, off_h: torch.Tensor, ids_h: torch.Tensor, kappa: int, k: int,
                     out_s_h: torch.Tensor | None = None, out_id_h: torch.Tensor | None = None, stream=None):
-        """Host-in, host-out search: copies the queries and candidate lists to the device,
-        searches, copies the top-k back (asynchronously on the stream when the host
-        tensors are pinned; call torch.cuda.synchronize / stream.synchronize to wait)."""
-        dev = self.X.device
-        st = stream if stream is not None else torch.cuda.current_stream()
-        with torch.cuda.stream(st):
-            key = (tuple(Q_h.shape), tuple(off_h.shape), tuple(ids_h.shape))
-            d = self._h2d.get(key)
-            if d is None:
-                d = (torch.empty(Q_h.shape, dtype=torch.float32, device=dev),
-                     torch.empty(off_h.shape, dtype=torch.int64, device=dev),
-                     torch.empty(ids_h.shape, dtype=torch.int32, device=dev))
-                self._h2d = {key: d}
-            Qd, offd, idsd = d
-            Qd.copy_(Q_h, non_blocking=True)
-            offd.copy_(off_h, non_blocking=True)
-            idsd.copy_(ids_h, non_blocking=True)
-            fs, fi = self.search(Qd, offd, idsd, kappa, k, stream=st)
-            if out_s_h is None:
-                out_s_h = torch.empty(fs.shape, dtype=fs.dtype, pin_memory=True)
-                out_id_h = torch.empty(fi.shape, dtype=fi.dtype, pin_memory=True)
-            out_s_h.copy_(fs, non_blocking=True)
-            out_id_h.copy_(fi, non_blocking=True)
+        """Host-in, host-out search through one library call (glv_search_host): the copies of
+        the queries and candidate lists in, the search and the copy of the top-k out are all
+        enqueued on the stream (asynchronous with pinned host tensors; synchronise the stream
+        before reading the outputs)."""
+        nq = Q_h.shape[0]
+        if out_s_h is None:
+            out_s_h = torch.empty(nq, k, dtype=torch.float32, pin_memory=True)
+            out_id_h = torch.empty(nq, k, dtype=torch.int32, pin_memory=True)
+        ws = self._host_workspace(nq, ids_h.shape[0], kappa, k, slot=0)
+        glv.glv_search_host(self.X, Q_h, self.A, self.compute, self.Xred, self.row_stride, self.scales, self.dt,
+                            self.tags, off_h, ids_h, kappa, k, ws, out_s_h, out_id_h, d_status=self.status,
+                            stream=stream)
         return out_s_h, out_id_h
+
+    def _host_workspace(self, nq: int, n_cand: int, kappa: int, k: int, slot: int):
+        key = (nq, n_cand, kappa, k, slot)
+        ws = self._h2d.get(key)
+        if ws is None:
+            nbytes = glv.search_host_workspace_bytes(nq, self.D, self.C, self.d, self.compute, n_cand, kappa, k)
+            ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.X.device)
+            self._h2d = {kk: v for kk, v in self._h2d.items() if kk[:4] == key[:4]}
+            self._h2d[key] = ws
+        return ws
 
     def device_status(self) -> int:
         """First device-side error recorded since the last reset (0 = none); synchronises."""
@@ -116,66 +116,48 @@ class GleanVecIndex:
 
 
 class HostSearchPipeline:
-    """Streams host-resident query batches through an index.
+    """Streams host-resident query batches through an index with the host-buffer entry point.
 
     ``submit`` enqueues one batch (pinned host tensors: queries, CSR candidate lists, and the
-    top-k outputs) and returns at once.  The host-to-device copies of a batch run on a copy
-    stream, so they overlap the search of the batch before it on the compute stream; the
-    top-k of each batch is copied back on the compute stream right after its search.
-    Device input buffers rotate over ``depth`` slots: a slot is refilled only after the
-    search that read it has finished.  ``synchronize`` waits for everything submitted.
+    top-k outputs) as one glv_search_host call and returns at once.  Batches rotate over
+    ``depth`` streams, each with its own device workspace, so the host-to-device copies of one
+    batch overlap the search of the batch before it; calls on the same stream (and so on the
+    same workspace) run in order.  ``synchronize`` waits for everything submitted.
     """
 
     def __init__(self, index: GleanVecIndex, kappa: int, k: int, depth: int = 2, stream=None):
         if depth < 2:
             raise ValueError("depth >= 2 (one batch copying while another is searched)")
         self.ix, self.kappa, self.k, self.depth = index, kappa, k, depth
-        self.compute = stream if stream is not None else torch.cuda.current_stream()
-        self.copy = torch.cuda.Stream(device=index.X.device)
-        self._slots = [None] * depth
-        self._done = [None] * depth
+        self.origin = stream if stream is not None else torch.cuda.current_stream()
+        self.streams = [torch.cuda.Stream(device=index.X.device) for _ in range(depth)]
         self._n = 0
 
-    def _slot(self, s: int, Q_h, off_h, ids_h):
-        key = (tuple(Q_h.shape), tuple(off_h.shape), tuple(ids_h.shape))
-        cur = self._slots[s]
-        if cur is None or cur[0] != key:
-            dev = self.ix.X.device
-            cur = (key, torch.empty(Q_h.shape, dtype=torch.float32, device=dev),
-                   torch.empty(off_h.shape, dtype=torch.int64, device=dev),
-                   torch.empty(ids_h.shape, dtype=torch.int32, device=dev))
-            self._slots[s] = cur
-        return cur[1:]
-
     def begin(self):
-        """Order the copy stream after the work already enqueued on the compute stream (for
-        timing: an event recorded on the compute stream before begin() precedes every
-        copy submitted after it)."""
-        self.copy.wait_stream(self.compute)
+        """Order every pipeline stream after the work already enqueued on the origin stream
+        (for timing: an event recorded there before begin() precedes every batch submitted
+        after it)."""
+        for st in self.streams:
+            st.wait_stream(self.origin)
 
     def submit(self, Q_h: torch.Tensor, off_h: torch.Tensor, ids_h: torch.Tensor, out_s_h: torch.Tensor,
                out_id_h: torch.Tensor) -> torch.cuda.Event:
         s = self._n % self.depth
         self._n += 1
-        Qd, offd, idsd = self._slot(s, Q_h, off_h, ids_h)
-        if self._done[s] is not None:
-            self.copy.wait_event(self._done[s])   # the search that last read this slot
-        with torch.cuda.stream(self.copy):
-            Qd.copy_(Q_h, non_blocking=True)
-            offd.copy_(off_h, non_blocking=True)
-            idsd.copy_(ids_h, non_blocking=True)
-            copied = torch.cuda.Event()
-            copied.record(self.copy)
-        self.compute.wait_event(copied)
-        with torch.cuda.stream(self.compute):
-            fs, fi = self.ix.search(Qd, offd, idsd, self.kappa, self.k, stream=self.compute)
-            out_s_h.copy_(fs, non_blocking=True)
-            out_id_h.copy_(fi, non_blocking=True)
-            done = torch.cuda.Event()
-            done.record(self.compute)
-        self._done[s] = done
+        st = self.streams[s]
+        ws = self.ix._host_workspace(Q_h.shape[0], ids_h.shape[0], self.kappa, self.k, slot=s)
+        ix = self.ix
+        glv.glv_search_host(ix.X, Q_h, ix.A, ix.compute, ix.Xred, ix.row_stride, ix.scales, ix.dt, ix.tags, off_h,
+                            ids_h, self.kappa, self.k, ws, out_s_h, out_id_h, d_status=ix.status, stream=st)
+        done = torch.cuda.Event()
+        done.record(st)
         return done
 
+    def end(self):
+        """Order the origin stream after every batch submitted so far."""
+        for st in self.streams:
+            self.origin.wait_stream(st)
+
     def synchronize(self):
-        self.compute.synchronize()
-        self.copy.synchronize()
+        for st in self.streams:
+            st.synchronize()

@@ -13,7 +13,8 @@ stand in for them with the same shapes and the same ID / OOD structure:
   ``alpha = 1``), every vector L2-normalised afterwards;
 * out-of-distribution queries: means ``R_o mu_k`` for one shared Haar rotation ``R_o``,
   fresh Haar bases, ``alpha = 0.5``, L2-normalised;
-* in-distribution queries: drawn from the database mixture itself;
+* in-distribution queries: drawn from the database mixture itself (``queries="ood+id"``: the
+  first half of the batch out-of-distribution, the second half in-distribution);
 * landmarks: ``C`` distinct database rows drawn uniformly (already unit norm);
 * projections: ``A_c = B_c = P_c`` with ``P_c`` a Haar-random row-orthonormal d x D
   matrix (QR of a Gaussian matrix, signs fixed by diag(R));
@@ -157,6 +158,11 @@ def make_workload(*, N: int, D: int, d: int, C: int, nq: int, K_db: int, cands,
         Q = mixture(nq, D, means @ Ro.T, 0.5, gq, device)
     elif queries == "id":
         Q = mixture(nq, D, means, 1.0, gq, device)
+    elif queries == "ood+id":  # first half out-of-distribution, second half in-distribution
+        Ro = haar_orthogonal(D, 1, gq, device)[0]
+        Qo = mixture(nq // 2, D, means @ Ro.T, 0.5, gq, device)
+        gi = _gen(seed_for(cfg, "queries") + 7 + 1_000_003 * replica, device)
+        Q = torch.cat([Qo, mixture(nq - nq // 2, D, means, 1.0, gi, device)])
     else:
         raise ValueError(queries)
 
@@ -189,8 +195,8 @@ WORKLOADS = {
                            kappa=0, k=10, cfg=0),
     "graph-1M-d160": dict(N=1_000_000, D=768, d=160, C=32, nq=10_000, K_db=64, cands=2048,
                           kappa=100, k=10, cfg=1),
-    "precision-10M-d128": dict(N=10_000_000, D=512, d=128, C=64, nq=10_000, K_db=64,
-                               cands=4096, kappa=200, k=10, cfg=2),
+    "precision-10M-d128": dict(N=10_000_000, D=512, d=128, C=64, nq=20_000, K_db=64,
+                               cands=4096, kappa=200, k=10, cfg=2, queries="ood+id"),
     "batching-2M-d192": dict(N=2_000_000, D=768, d=192, C=48, nq=8192, K_db=64,
                              cands=("lognormal", 2000.0, 1.2, 64, 32768), kappa=100, k=10,
                              cfg=3),
@@ -198,7 +204,8 @@ WORKLOADS = {
 
 
 def workload(name: str, device="cpu", **override) -> Workload:
-    """One of the named workloads, drawn on ``device``; keyword overrides change its fields."""
+    """One of the named workloads, drawn on ``device``; keyword overrides change its fields
+    (``queries=None`` keeps the workload's own query mix)."""
     kw = dict(WORKLOADS[name])
-    kw.update(override)
+    kw.update({k: v for k, v in override.items() if v is not None})
     return make_workload(device=device, name=name, **kw)

@@ -517,3 +517,25 @@ def test_spherical_kmeans_em_is_monotone():
         mu = mu64.astype(np.float32)
         prev = oracle.spherical_objective(X, mu, tags)
         assert prev >= obj_e - 1e-4      # the M-step does not lower the objective
+
+
+# ---------------------------------------------------------------------------------------
+# recall (Section 5: k-recall@k = |S cap G| / k, averaged over queries)
+# ---------------------------------------------------------------------------------------
+
+def test_recall_hand_counted():
+    """Counted by hand: query 0 finds {2, 3} of its truth {3, 2, 9, 10} (its -1 slot is empty);
+    query 1 finds all four of {8, 7, 6, 5} in another order; (2 + 4) / (4 * 2) = 0.75."""
+    found = [[1, 2, 3, -1], [5, 6, 7, 8]]
+    truth = [[3, 2, 9, 10], [8, 7, 6, 5]]
+    assert oracle.recall(found, truth) == 0.75
+
+
+def test_recall_uses_the_truth_width_and_ignores_empty_slots():
+    # K is the truth's width (here 2), even when more ids were returned
+    assert oracle.recall([[4, 5, 6]], [[6, 9]]) == 0.5
+    # -1 marks an empty slot on either side and never counts as a hit
+    assert oracle.recall([[-1, -1]], [[-1, -1]]) == 0.0
+    assert oracle.recall([[7, -1]], [[7, -1]]) == 0.5
+    # duplicates are not counted twice
+    assert oracle.recall([[7, 7]], [[7, 8]]) == 0.5
