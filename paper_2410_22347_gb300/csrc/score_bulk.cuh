@@ -132,7 +132,7 @@ GLV_DEV bool score_range_bulk(const ScoreArgs& a, const float* qs, uint8_t* ring
             sv = -INFINITY;
             report(a.d_status, GLV_ERR_BAD_ID);
           } else if constexpr (DT == GLV_FP8_E4M3) {
-            sv = (acc * 0x1p120f) * sc;
+            sv = (acc * qp_scales(a, qs)[tag]) * sc;
           } else {
             sv = acc;
           }

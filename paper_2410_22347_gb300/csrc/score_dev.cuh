@@ -5,11 +5,15 @@
 // A group of G lanes scores one candidate: the lanes issue all of their 16-byte loads of
 // the reduced row (NCH each) before any arithmetic, so a warp keeps 32 x NCH x 16 bytes in
 // flight; partial dots are combined with xor-shuffles inside the group.  Rows are decoded in
-// registers: FP32 as is, BF16 by shifting into the high half of an FP32 word, FP8-e4m3 by
-// moving sign / exponent / mantissa bits into an FP32 word, which yields
-// decode(code) * 2^-120 for normal and subnormal codes alike; the 2^120 factor and the row
-// scale are applied once to the finished dot.
+// registers: FP32 as is, BF16 by shifting into the high half of an FP32 word.  FP8-e4m3 codes
+// are converted two at a time to f16 (exact: every e4m3 value is an f16 value) and multiplied
+// with mixed-precision FMAs (f16 x f16 products, FP32 accumulation) against the projected
+// query held as two f16 terms per element, q * 2^sigma_c = hi + lo (22 significant bits; the
+// power of two 2^sigma_c per cluster keeps both terms in f16's normal range).  The cluster's
+// 2^-sigma_c and the row scale are applied once to the finished dot.
 #pragma once
+
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -34,11 +38,35 @@ struct Elem<GLV_FP8_E4M3> {
   static constexpr int kBytes = 1;
 };
 
-// FP8-e4m3 byte (bits 24..31 of t) -> FP32 word with the same sign, the 4 exponent bits as
-// the low bits of the FP32 exponent field and the 3 mantissa bits on top of the FP32
-// mantissa: value = decode(byte) * 2^-120 (exact, including subnormal codes).
-GLV_DEV float e4m3_hi_byte_scaled(uint32_t t) {
-  return __uint_as_float((t & 0x80000000u) | ((t & 0x7f000000u) >> 4));
+// Four FP8-e4m3 codes (the bytes of x, element 0 in the low byte) against the projected-query
+// terms of the same four elements, q = [hi(0,1), hi(2,3), lo(0,1), lo(2,3)] as f16 pairs:
+// sh += sum_e x_e * hi_e, sl += sum_e x_e * lo_e, element by element in order (each product
+// exact, each sum rounded to FP32).
+GLV_DEV void fp8_word_dot(uint32_t x, float4 q, float& sh, float& sl) {
+  asm("{\n\t"
+      ".reg .b16 c01, c23, x0, x1, x2, x3, h0, h1, h2, h3, l0, l1, l2, l3;\n\t"
+      ".reg .b32 p01, p23;\n\t"
+      "mov.b32 {c01, c23}, %2;\n\t"
+      "cvt.rn.f16x2.e4m3x2 p01, c01;\n\t"
+      "cvt.rn.f16x2.e4m3x2 p23, c23;\n\t"
+      "mov.b32 {x0, x1}, p01;\n\t"
+      "mov.b32 {x2, x3}, p23;\n\t"
+      "mov.b32 {h0, h1}, %3;\n\t"
+      "mov.b32 {h2, h3}, %4;\n\t"
+      "mov.b32 {l0, l1}, %5;\n\t"
+      "mov.b32 {l2, l3}, %6;\n\t"
+      "fma.rn.f32.f16 %0, x0, h0, %0;\n\t"
+      "fma.rn.f32.f16 %1, x0, l0, %1;\n\t"
+      "fma.rn.f32.f16 %0, x1, h1, %0;\n\t"
+      "fma.rn.f32.f16 %1, x1, l1, %1;\n\t"
+      "fma.rn.f32.f16 %0, x2, h2, %0;\n\t"
+      "fma.rn.f32.f16 %1, x2, l2, %1;\n\t"
+      "fma.rn.f32.f16 %0, x3, h3, %0;\n\t"
+      "fma.rn.f32.f16 %1, x3, l3, %1;\n\t"
+      "}"
+      : "+f"(sh), "+f"(sl)
+      : "r"(x), "r"(__float_as_uint(q.x)), "r"(__float_as_uint(q.y)), "r"(__float_as_uint(q.z)),
+        "r"(__float_as_uint(q.w)));
 }
 
 // Dot product of one 16-byte chunk of a reduced row with the matching projected-query
@@ -78,17 +106,17 @@ GLV_DEV float dot_chunk(uint4 v, const float* qrow, int ch, int sbs, int sw) {
       s = fmaf(b.z, __uint_as_float(x3 << 16), s);
       s = fmaf(b.w, __uint_as_float(x3 & 0xffff0000u), s);
     } else {
-      // sub-block t holds the four bytes of word t; odd groups take them in the order 2, 3, 0, 1
+      // sub-block t holds the terms of the four elements of word t as f16 pairs
+      // [hi(0,1), hi(2,3), lo(0,1), lo(2,3)]; odd groups take the words in the order 2, 3, 0, 1.
+      // The hi and lo products accumulate in two chains, added at the end.
       const uint32_t xs[4] = {x0, x1, x2, x3};
+      float sl = 0.f;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const float4 a = q4[(t ^ (sw << 1)) * sbs + ch];
-        const uint32_t x = xs[t];
-        s = fmaf(a.x, e4m3_hi_byte_scaled(x << 24), s);
-        s = fmaf(a.y, e4m3_hi_byte_scaled(x << 16), s);
-        s = fmaf(a.z, e4m3_hi_byte_scaled(x << 8), s);
-        s = fmaf(a.w, e4m3_hi_byte_scaled(x), s);
+        fp8_word_dot(xs[t], a, s, sl);
       }
+      s += sl;
     }
     return s;
   }
@@ -107,9 +135,9 @@ GLV_DEV uint4 keep_bytes(uint4 v, int nbytes) {
 }
 
 // Stage the C projected views of query j into shared memory in the sub-block layout of
-// dot_chunk (rows of a.qstride floats; elements d..dpad-1 are zero).
+// dot_chunk as FP32 values (rows of a.qstride floats; elements d..dpad-1 are zero).
 template <int DT>
-GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
+GLV_DEV void stage_qp_f32(const ScoreArgs& a, int64_t j, float* qs) {
   constexpr int EPC = Elem<DT>::kPerChunk;
   const float* qj = a.Qp + j * (int64_t)a.C * a.d;
   const int dpad = a.nch * EPC;
@@ -147,6 +175,77 @@ GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
   }
 }
 
+GLV_DEV float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// FP8 rows: the per-cluster factors 2^-sigma_c follow the C rows of projected views.
+GLV_DEV float* qp_scales(const ScoreArgs& a, float* qs) { return qs + (size_t)a.C * a.qstride; }
+GLV_DEV const float* qp_scales(const ScoreArgs& a, const float* qs) { return qs + (size_t)a.C * a.qstride; }
+
+// FP8 rows: turn the FP32 projected views staged in the sub-block layout into the f16 term
+// pairs dot_chunk reads, in place, one warp per cluster row (rows with seen[c] == 0 skipped
+// when seen is given).  sigma_c = 14 - floor(log2 max_e |q_c,e|) (clamped to +-126) puts the
+// largest |q| * 2^sigma_c in [2^14, 2^15); hi = f16(q 2^sigma_c), lo = f16(q 2^sigma_c - hi)
+// (the difference is exact in FP32), so hi + lo holds q 2^sigma_c to 22 significant bits.
+// Each 16-byte slot holding elements 4t..4t+3 of a chunk becomes
+// [hi(0,1), hi(2,3), lo(0,1), lo(2,3)], and 2^-sigma_c goes to qp_scales.
+GLV_DEV void split_qp_fp8(const ScoreArgs& a, float* qs, const uint8_t* seen) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int slots = a.nch * 4;  // 16-byte slots per row: 4 sub-blocks of nch chunks
+  float* qsc = qp_scales(a, qs);
+  for (int c = warp; c < a.C; c += nwarps) {
+    if (seen && !seen[c]) continue;
+    float4* row = reinterpret_cast<float4*>(qs + (size_t)c * a.qstride);
+    float m = 0.f;
+    for (int t = lane; t < slots; t += 32) {
+      const int u = t / a.nch, ch = t - u * a.nch;
+      const float4 v = row[u * a.sbs + ch];
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    m = warp_max(m);
+    int sigma = 0;
+    if (m > 0.f && m <= 3.4e38f) {
+      const int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m); -127 if subnormal
+      sigma = min(126, max(-126, 14 - e));
+    }
+    const float up = __uint_as_float((uint32_t)(127 + sigma) << 23);
+    const float down = __uint_as_float((uint32_t)(127 - sigma) << 23);
+    for (int t = lane; t < slots; t += 32) {
+      const int u = t / a.nch, ch = t - u * a.nch;
+      const float4 v = row[u * a.sbs + ch];
+      const float f[4] = {v.x * up, v.y * up, v.z * up, v.w * up};
+      __half h[4], l[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        h[k] = __float2half_rn(f[k]);
+        l[k] = __float2half_rn(f[k] - __half2float(h[k]));
+      }
+      float4 o;
+      o.x = __uint_as_float((uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16));
+      o.y = __uint_as_float((uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16));
+      o.z = __uint_as_float((uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16));
+      o.w = __uint_as_float((uint32_t)__half_as_ushort(l[2]) | ((uint32_t)__half_as_ushort(l[3]) << 16));
+      row[u * a.sbs + ch] = o;
+    }
+    if (lane == 0) qsc[c] = down;
+  }
+}
+
+// Stage the C projected views of query j into shared memory in the sub-block layout of
+// dot_chunk (rows of a.qstride floats; elements d..dpad-1 are zero); FP8 rows then get their
+// f16 term pairs (split_qp_fp8).  Called by the whole CTA.
+template <int DT>
+GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
+  stage_qp_f32<DT>(a, j, qs);
+  if constexpr (DT == GLV_FP8_E4M3) {
+    __syncthreads();
+    split_qp_fp8(a, qs, nullptr);
+  }
+}
+
 // 16-byte asynchronous copy global -> shared that bypasses L1 (cp.async.cg); src_bytes < 16
 // fills the rest of the 16 bytes with zeros.  Completes at cp_async_wait_all.
 GLV_DEV void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
@@ -154,9 +253,11 @@ GLV_DEV void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
 }
 
-// Whether stage_qp_async can stage this problem's projected views (the float4 layout).
+// Whether stage_qp_async can stage this problem's projected views (the float4 layout; FP8
+// rows need the f16 terms computed, so they are staged by stage_qp).
+template <int DT>
 GLV_DEV bool qp_async_ok(const ScoreArgs& a) {
-  return (a.d & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Qp) & 15) == 0;
+  return DT != GLV_FP8_E4M3 && (a.d & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Qp) & 15) == 0;
 }
 
 // stage_qp's float4 path as asynchronous copies: every float4 of the query's C projected views
@@ -229,7 +330,7 @@ GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, 
       s = -INFINITY;
       report(a.d_status, GLV_ERR_BAD_ID);
     } else if constexpr (DT == GLV_FP8_E4M3) {
-      s = (acc * 0x1p120f) * r.sc;
+      s = (acc * qp_scales(a, qs)[r.tag]) * r.sc;
     } else {
       s = acc;
     }

@@ -27,7 +27,8 @@ struct ScoreSmem {
 __host__ __device__ inline ScoreSmem score_smem(int C, int qstride, bool fused, int mode, int RB, int nch,
                                                 int kappa = 0) {
   ScoreSmem m;
-  m.qs_bytes = (((size_t)C * qstride * sizeof(float)) + 127) & ~size_t(127);
+  // the C rows of projected views, then C per-cluster factors (used by FP8 rows)
+  m.qs_bytes = (((size_t)C * (qstride + 1) * sizeof(float)) + 127) & ~size_t(127);
   m.keys_bytes = fused ? (((size_t)kFusedCache * sizeof(uint32_t) + (size_t)kappa * 8) + 127) & ~size_t(127) : 0;
   const int warps = kScoreThreads / 32;
   m.ring_bytes = mode == 2 ? (size_t)warps * kBulkSlots * RB * nch * 16 : 0;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
         if (id >= 0 && id < a.N) prefetch_l2_bulk(a.Xred + id * a.row_stride, (uint32_t)a.row_stride);
       }
       const int64_t qbytes = (int64_t)a.C * a.d * 4;
-      if (nq != j && qp_async_ok(a)) {
+      if (nq != j && qp_async_ok<DT>(a)) {
         stage_qp_async<DT>(a, nq, qs);
         if (threadIdx.x == 0) s_staged = nq;  // read again only after the selection's barriers
       } else if (nq != j && (qbytes & 15) == 0) {

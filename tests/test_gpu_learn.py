@@ -163,7 +163,10 @@ def test_backward_matches_exact_central_differences_of_the_fp64_loss(learn):
 
 
 def test_pair_loss_weight_scales_the_gradient(learn):
-    """The upstream weight multiplies g on the device: backward of 3 L is 3x backward of L."""
+    """The upstream weight multiplies g on the device: the backward of 4 L is 4 times the
+    backward of L (a power of two scales every rounded term exactly; the pairs of a cluster are
+    summed in the order the device grouping left them, which may differ between the calls, so
+    the sums agree to FP32 summation error)."""
     D, d, C, P = 32, 8, 2, 700
     rng, Q, X, mu = _sets(19, D, 100, 900, C)
     tags = _t(oracle.assign_tags(X, mu))
@@ -172,12 +175,12 @@ def test_pair_loss_weight_scales_the_gradient(learn):
     qi = _t(rng.integers(0, 100, P).astype(np.int32))
     xi = _t(rng.integers(0, 900, P).astype(np.int32))
     grads = []
-    for wgt in (1.0, 3.0):
+    for wgt in (1.0, 4.0):
         A1, B1 = A.clone().requires_grad_(True), B.clone().requires_grad_(True)
         (wgt * learn.pair_loss(A1, B1, _t(Q), _t(X), tags, qi, xi)).backward()
         grads.append((A1.grad.clone(), B1.grad.clone()))
-    for g1, g3 in zip(grads[0], grads[1]):
-        torch.testing.assert_close(g3, 3.0 * g1, rtol=1e-6, atol=0)
+    for g1, g4 in zip(grads[0], grads[1]):
+        torch.testing.assert_close(g4, 4.0 * g1, rtol=0, atol=1e-5 * float((4.0 * g1).abs().max()))
 
 
 def test_adam_step_matches_the_textbook_update(learn):
