@@ -7,8 +7,8 @@
 //           mantissa bits cleared (exactly representable in TF32), lo = value - hi; three
 //           kind::tf32 MMAs per K-step accumulate hi*hi + hi*lo + lo*hi, which reproduces the
 //           FP32 product to ~2^-20 relative (lo*lo is below that).  This is the FP32 mode.
-// A small prep kernel writes the converted / split operands (rows padded with zeros to a
-// multiple of 64 along K) into the caller's workspace; TMA then streams 128-byte-wide K
+// One prep launch writes the converted / split operands of Q and A (rows padded with zeros to
+// a multiple of 64 along K) into the caller's workspace; TMA then streams 128-byte-wide K
 // slices into shared memory in the 128-byte swizzled layout the MMA descriptors expect.
 //
 // Kernel structure (one persistent CTA per SM, 10 warps):
@@ -18,8 +18,10 @@
 //               MMAs of tile t+1;
 //   warps 2..9  epilogue, two warps per TMEM lane quadrant (each half of the columns):
 //               tcgen05.ld 32 lanes x 32 columns at a time (the next chunk's load in flight
-//               while this one is stored), transposed through a padded shared-memory tile ->
-//               coalesced FP32 global stores (128 B per row).
+//               while this one is stored), written to a 4-KB shared-memory tile in the
+//               128-byte swizzled layout and sent to Qp by one TMA tensor store per chunk (or,
+//               when Qp's rows are not 16-byte multiples, transposed through a padded tile and
+//               written by coalesced store instructions).
 // Every mbarrier wait is bounded (see tc.cuh); a timeout sets GLV_ERR_TIMEOUT in d_status,
 // all roles leave their loops, outstanding TMA loads and MMAs are drained (bounded), and the
 // TMEM is freed before the CTA exits.
@@ -53,9 +55,10 @@ struct TcCfg {
   static constexpr int kKPerStage = kTcRowBytes / kElemBytes;
   static constexpr int kKPerMma = MODE == 0 ? 16 : 8;     // 32 bytes of K per MMA
   static constexpr int kMmaPerStage = kKPerStage / kKPerMma;
-  // epilogue staging: per epilogue warp a 32 x 32 FP32 tile, rows padded to 33 words
+  // epilogue staging: per epilogue warp a 32 x 32 FP32 tile -- rows padded to 33 words for the
+  // store-instruction path, or 4 KB in the 128-byte swizzled layout of a TMA tensor store
   static constexpr size_t kEpiBytes = (size_t)kTcEpiWarps * 32 * 33 * sizeof(float);
-  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 + 256 + kEpiBytes;
+  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + kEpiBytes + 256 + 1024;
 };
 
 struct TcArgs {
@@ -66,24 +69,26 @@ struct TcArgs {
   int tiles_n;
   int64_t num_tiles;
   int32_t* d_status;
+  int tma_store;    // 1: the epilogue writes Qp with TMA tensor stores (tmOut)
 };
 
 template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
     project_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                       const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
-                      const TcArgs args) {
+                      const __grid_constant__ CUtensorMap tmOut, const TcArgs args) {
   using Cfg = TcCfg<MODE>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)Cfg::kStages * Cfg::kStageBytes);
+  // [stages | epilogue staging (1024-aligned) | barriers]
+  float* epi = reinterpret_cast<float*>(smem + (size_t)Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)Cfg::kStages * Cfg::kStageBytes + Cfg::kEpiBytes);
   uint64_t* empty = full + Cfg::kStages;
   uint64_t* tfull = empty + Cfg::kStages;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* epi = reinterpret_cast<float*>(smem + (size_t)Cfg::kStages * Cfg::kStageBytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -100,6 +105,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_mbar_init();
     tc::prefetch_tmap(&tmA0);
     tc::prefetch_tmap(&tmB0);
+    if (args.tma_store) tc::prefetch_tmap(&tmOut);
     if (MODE == 1) {
       tc::prefetch_tmap(&tmA1);
       tc::prefetch_tmap(&tmB1);
@@ -234,6 +240,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t r[32];
       tc::tmem_ld_32x32b_x32(tbase, r);
       tc::tmem_ld_wait(r);
+      if (args.tma_store) {
+        // each 32 x 32 chunk goes to the warp's 4-KB staging tile in the 128-byte swizzled layout
+        // (row = lane, 16-byte piece c at position c ^ (row & 7): the eight lanes of a quarter
+        // warp hit eight different bank groups) and leaves with one TMA tensor store; rows or
+        // columns beyond Qp's bounds are clipped by the TMA unit
+        uint8_t* tile = reinterpret_cast<uint8_t*>(epi) + (size_t)(warp - 2) * 4096;
+#pragma unroll 1
+        for (int ch = 0; ch < kChunks; ++ch) {
+          if (lane == 0) tc::tma_store_wait_read();  // the previous chunk's store has read the tile
+          __syncwarp();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint4 v = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+            *reinterpret_cast<uint4*>(tile + lane * 128 + ((c ^ (lane & 7)) << 4)) = v;
+          }
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (ch + 1 < kChunks) tc::tmem_ld_32x32b_x32(tbase + (uint32_t)((ch + 1) * 32), r);
+          if (lane == 0) {
+            tc::tma_store_2d(&tmOut, tn * kTcBN + (ch0 + ch) * 32, (int)row_base, tile);
+            tc::tma_store_commit();
+          }
+          tc::tmem_ld_wait(r);
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&tempty[acc]);
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1;
+        continue;
+      }
 #pragma unroll 1
       for (int ch = 0; ch < kChunks; ++ch) {
 #pragma unroll
@@ -258,6 +294,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   }
 
+  if (warp >= 2 && lane == 0 && args.tma_store) tc::tma_store_wait_all();  // Qp written before exit
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -269,15 +306,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ---- operand preparation -------------------------------------------------------------------
 
-// One thread per 4 consecutive K elements of a row; Kp is a multiple of 64, so a group never
-// straddles rows.  Reads are 16-byte vectors when D % 4 == 0.
-__global__ void prep_bf16_kernel(const float* __restrict__ src, int64_t rows, int D, int Kp,
-                                 __nv_bfloat16* __restrict__ dst) {
+// Both operands in one launch: one thread per 4 consecutive K elements of a row, the rows of
+// Q first, then those of A; Kp is a multiple of 64, so a group never straddles rows.  Reads
+// are 16-byte vectors when D % 4 == 0.
+struct PrepPair {
+  const float* src[2];
+  int64_t rows[2];
+};
+
+__global__ void prep_bf16_kernel(PrepPair pp, int D, int Kp, __nv_bfloat16* __restrict__ dst0,
+                                 __nv_bfloat16* __restrict__ dst1) {
   const int gpr = Kp / 4;
-  const int64_t total = rows * (int64_t)gpr;
+  const int64_t first = pp.rows[0] * (int64_t)gpr;
+  const int64_t total = first + pp.rows[1] * (int64_t)gpr;
   const bool vec = (D % 4) == 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < total;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int w = i0 < first ? 0 : 1;
+    const int64_t i = w ? i0 - first : i0;
+    const float* src = pp.src[w];
+    __nv_bfloat16* dst = w ? dst1 : dst0;
     const int64_t r = i / gpr;
     const int k = (int)(i - r * gpr) * 4;
     float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -298,13 +346,19 @@ __global__ void prep_bf16_kernel(const float* __restrict__ src, int64_t rows, in
   }
 }
 
-__global__ void prep_tf32x3_kernel(const float* __restrict__ src, int64_t rows, int D, int Kp,
-                                   float* __restrict__ hi, float* __restrict__ lo) {
+__global__ void prep_tf32x3_kernel(PrepPair pp, int D, int Kp, float* __restrict__ hi0, float* __restrict__ lo0,
+                                   float* __restrict__ hi1, float* __restrict__ lo1) {
   const int gpr = Kp / 4;
-  const int64_t total = rows * (int64_t)gpr;
+  const int64_t first = pp.rows[0] * (int64_t)gpr;
+  const int64_t total = first + pp.rows[1] * (int64_t)gpr;
   const bool vec = (D % 4) == 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < total;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int w = i0 < first ? 0 : 1;
+    const int64_t i = w ? i0 - first : i0;
+    const float* src = pp.src[w];
+    float* hi = w ? hi1 : hi0;
+    float* lo = w ? lo1 : lo0;
     const int64_t r = i / gpr;
     const int k = (int)(i - r * gpr) * 4;
     float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -389,12 +443,16 @@ cudaError_t launch_project_tc(const float* Q, int64_t nq, int D, const float* A,
     p += abytes;
   }
   const int pb = num_sms * 8;
+  PrepPair pp;
+  pp.src[0] = Q;
+  pp.rows[0] = nq;
+  pp.src[1] = A;
+  pp.rows[1] = Mc;
   if (bf16) {
-    prep_bf16_kernel<<<pb, 256, 0, st>>>(Q, nq, D, Kp, static_cast<__nv_bfloat16*>(q0));
-    prep_bf16_kernel<<<pb, 256, 0, st>>>(A, Mc, D, Kp, static_cast<__nv_bfloat16*>(a0));
+    prep_bf16_kernel<<<pb, 256, 0, st>>>(pp, D, Kp, static_cast<__nv_bfloat16*>(q0), static_cast<__nv_bfloat16*>(a0));
   } else {
-    prep_tf32x3_kernel<<<pb, 256, 0, st>>>(Q, nq, D, Kp, static_cast<float*>(q0), static_cast<float*>(q1));
-    prep_tf32x3_kernel<<<pb, 256, 0, st>>>(A, Mc, D, Kp, static_cast<float*>(a0), static_cast<float*>(a1));
+    prep_tf32x3_kernel<<<pb, 256, 0, st>>>(pp, D, Kp, static_cast<float*>(q0), static_cast<float*>(q1),
+                                           static_cast<float*>(a0), static_cast<float*>(a1));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -410,7 +468,24 @@ cudaError_t launch_project_tc(const float* Q, int64_t nq, int D, const float* A,
     return cudaErrorInvalidValue;
   }
 
+  // Qp written by TMA tensor stores when its rows are 16-byte multiples (32 x 32 FP32 boxes,
+  // 128-byte swizzle), else by store instructions
+  CUtensorMap mOut;
+  bool tma_store = (Mc % 4) == 0 && (reinterpret_cast<uintptr_t>(Qp) % 16) == 0;
+  if (tma_store) {
+    auto enc = tensor_map_encoder();
+    cuuint64_t dims[2] = {(cuuint64_t)Mc, (cuuint64_t)nq};
+    cuuint64_t strides[1] = {(cuuint64_t)Mc * 4};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    tma_store = enc && enc(&mOut, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Qp, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  if (!tma_store) mOut = mA0;  // unused
+
   TcArgs args;
+  args.tma_store = tma_store ? 1 : 0;
   args.out = Qp;
   args.M = nq;
   args.N = Mc;
@@ -423,12 +498,12 @@ cudaError_t launch_project_tc(const float* Q, int64_t nq, int D, const float* A,
     auto k = project_tc_kernel<0>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<0>::kSmem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kTcThreads, TcCfg<0>::kSmem, st>>>(mA0, mA1, mB0, mB1, args);
+    k<<<grid, kTcThreads, TcCfg<0>::kSmem, st>>>(mA0, mA1, mB0, mB1, mOut, args);
   } else {
     auto k = project_tc_kernel<1>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<1>::kSmem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kTcThreads, TcCfg<1>::kSmem, st>>>(mA0, mA1, mB0, mB1, args);
+    k<<<grid, kTcThreads, TcCfg<1>::kSmem, st>>>(mA0, mA1, mB0, mB1, mOut, args);
   }
   return cudaGetLastError();
 }

@@ -13,15 +13,36 @@
 
 namespace glv {
 
-extern template cudaError_t launch_score_dt<GLV_F32>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
-extern template cudaError_t launch_score_dt<GLV_BF16>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
-extern template cudaError_t launch_score_dt<GLV_FP8_E4M3>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
-extern template cudaError_t launch_fused_dt<GLV_F32>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*,
-                                                     int32_t*, ScoreConfig, cudaStream_t);
-extern template cudaError_t launch_fused_dt<GLV_BF16>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*,
-                                                      int32_t*, ScoreConfig, cudaStream_t);
-extern template cudaError_t launch_fused_dt<GLV_FP8_E4M3>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*,
-                                                          int32_t*, ScoreConfig, cudaStream_t);
+// each (store type, gather mode) pair is instantiated in its own translation unit
+#define GLV_EXTERN_MODES(DT)                                                                                     \
+  extern template cudaError_t launch_score_mode<DT, 0>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t); \
+  extern template cudaError_t launch_score_mode<DT, 1>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t); \
+  extern template cudaError_t launch_score_mode<DT, 2>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t); \
+  extern template cudaError_t launch_fused_mode<DT, 0>(const ScoreArgs&, unsigned, int, const ChunkPlan&,       \
+                                                       float*, int32_t*, ScoreConfig, cudaStream_t);            \
+  extern template cudaError_t launch_fused_mode<DT, 1>(const ScoreArgs&, unsigned, int, const ChunkPlan&,       \
+                                                       float*, int32_t*, ScoreConfig, cudaStream_t);
+GLV_EXTERN_MODES(GLV_F32)
+GLV_EXTERN_MODES(GLV_BF16)
+GLV_EXTERN_MODES(GLV_FP8_E4M3)
+
+template <int DT>
+static cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, int RB, ScoreConfig cfg, cudaStream_t st) {
+  switch (cfg.mode) {
+    case 1: return launch_score_mode<DT, 1>(a, grid, RB, cfg, st);
+    case 2: return launch_score_mode<DT, 2>(a, grid, RB, cfg, st);
+    default: return launch_score_mode<DT, 0>(a, grid, RB, cfg, st);
+  }
+}
+
+template <int DT>
+static cudaError_t launch_fused_dt(const ScoreArgs& a, unsigned grid, int kappa, const ChunkPlan& plan, float* out_s,
+                                   int32_t* out_id, ScoreConfig cfg, cudaStream_t st) {
+  switch (cfg.mode) {
+    case 1: return launch_fused_mode<DT, 1>(a, grid, kappa, plan, out_s, out_id, cfg, st);
+    default: return launch_fused_mode<DT, 0>(a, grid, kappa, plan, out_s, out_id, cfg, st);  // bulk (2) -> 0
+  }
+}
 
 constexpr size_t kScoreSmemLimit = 227 * 1024 - 12 * 1024;  // leaves room for static shared memory
 

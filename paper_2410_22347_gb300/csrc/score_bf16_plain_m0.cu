@@ -1,0 +1,7 @@
+// score_bf16_plain_m0.cu -- stand-alone scoring kernels of the GLV_BF16 reduced-row store, gather mode 0
+// (register row loads), instantiated for every lane count and row width.
+#include "score_variants.cuh"
+
+namespace glv {
+GLV_INSTANTIATE_SCORE_PLAIN(GLV_BF16, 0)
+}  // namespace glv

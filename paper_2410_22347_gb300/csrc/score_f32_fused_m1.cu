@@ -1,0 +1,7 @@
+// score_f32_fused_m1.cu -- fused scoring + top-kappa kernels of the GLV_F32 reduced-row store, gather mode 1
+// (pipelined register row loads), instantiated for every lane count and row width.
+#include "score_variants.cuh"
+
+namespace glv {
+GLV_INSTANTIATE_SCORE_FUSED(GLV_F32, 1)
+}  // namespace glv

@@ -1,0 +1,7 @@
+// score_f32_plain_m0.cu -- stand-alone scoring kernels of the GLV_F32 reduced-row store, gather mode 0
+// (register row loads), instantiated for every lane count and row width.
+#include "score_variants.cuh"
+
+namespace glv {
+GLV_INSTANTIATE_SCORE_PLAIN(GLV_F32, 0)
+}  // namespace glv

@@ -1,0 +1,7 @@
+// score_fp8_fused_m1.cu -- fused scoring + top-kappa kernels of the GLV_FP8_E4M3 reduced-row store, gather mode 1
+// (pipelined register row loads), instantiated for every lane count and row width.
+#include "score_variants.cuh"
+
+namespace glv {
+GLV_INSTANTIATE_SCORE_FUSED(GLV_FP8_E4M3, 1)
+}  // namespace glv

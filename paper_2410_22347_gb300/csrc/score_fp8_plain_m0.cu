@@ -1,0 +1,7 @@
+// score_fp8_plain_m0.cu -- stand-alone scoring kernels of the GLV_FP8_E4M3 reduced-row store, gather mode 0
+// (register row loads), instantiated for every lane count and row width.
+#include "score_variants.cuh"
+
+namespace glv {
+GLV_INSTANTIATE_SCORE_PLAIN(GLV_FP8_E4M3, 0)
+}  // namespace glv

@@ -4,8 +4,10 @@
 // For a row of nch 16-byte chunks and G lanes per candidate, every lane loads
 // NCH = ceil(nch / G) chunks.  Gather modes: 0 = row loads into registers, 1 = the same with
 // the next candidate's loads issued before the current dot (pipelined), 2 = bulk copies of
-// whole rows into shared memory (score_bulk.cuh).  Instantiated: NCH in {1..6, 8, 10} for
-// modes 0 and 2, NCH <= 5 for mode 1; G in the store type's three group sizes plus 32.
+// whole rows into shared memory (score_bulk.cuh; stand-alone kernel only).  Instantiated:
+// NCH in {1..6, 8, 10} for modes 0 and 2, NCH <= 5 for mode 1; G in the store type's three
+// group sizes plus 32.  Each (store type, kernel, mode) is compiled in its own translation
+// unit (score_<type>_<plain|fused>_m<mode>.cu).
 #pragma once
 
 #include "kernels.cuh"
@@ -24,6 +26,19 @@ struct Groups {
 inline bool nch_supported(int n, int mode) {
   if (mode == 1) return n >= 1 && n <= 5;
   return (n >= 1 && n <= 6) || n == 8 || n == 10;
+}
+
+// Whether a configuration (G, mode) is instantiated for store type DT.
+template <int DT>
+inline bool group_supported(int G, int mode) {
+  (void)mode;
+  return G == Groups<DT>::kLo || G == Groups<DT>::G0 || G == Groups<DT>::kHi || G == 32;
+}
+
+// Smallest instantiated NCH >= n (extra slots are predicated off).
+inline int round_nch(int n, int mode) {
+  while (n <= 10 && !nch_supported(n, mode)) ++n;
+  return n;
 }
 
 template <int DT, int G, int MODE, class F>
@@ -47,27 +62,15 @@ cudaError_t dispatch_nch_mode(int n, F& f) {
   return cudaErrorInvalidValue;
 }
 
-// Call f.template go<DT, G, NCH, MODE>() for the requested configuration.
-template <int DT, int G, class F>
-cudaError_t dispatch_nch(int n, int mode, F& f) {
-  if (mode == 1) return dispatch_nch_mode<DT, G, 1>(n, f);
-  if (mode == 2) return dispatch_nch_mode<DT, G, 2>(n, f);
-  return dispatch_nch_mode<DT, G, 0>(n, f);
-}
-
-// Smallest instantiated NCH >= n (extra slots are predicated off).
-inline int round_nch(int n, int mode) {
-  while (n <= 10 && !nch_supported(n, mode)) ++n;
-  return n;
-}
-
-template <int DT, class F>
-cudaError_t dispatch_score(int G, int nch, int mode, F& f) {
-  const int n = round_nch((nch + G - 1) / G, mode);
-  if (G == Groups<DT>::kLo) return dispatch_nch<DT, Groups<DT>::kLo>(n, mode, f);
-  if (G == Groups<DT>::G0) return dispatch_nch<DT, Groups<DT>::G0>(n, mode, f);
-  if (G == Groups<DT>::kHi) return dispatch_nch<DT, Groups<DT>::kHi>(n, mode, f);
-  if (G == 32) return dispatch_nch<DT, 32>(n, mode, f);
+// Call f.template go<DT, G, NCH, MODE>() for the lane count G of one gather mode.
+template <int DT, int MODE, class F>
+cudaError_t dispatch_score_mode(int G, int nch, F& f) {
+  using Gs = Groups<DT>;
+  const int n = round_nch((nch + G - 1) / G, MODE);
+  if (G == Gs::kLo) return dispatch_nch_mode<DT, Gs::kLo, MODE>(n, f);
+  if (G == Gs::G0) return dispatch_nch_mode<DT, Gs::G0, MODE>(n, f);
+  if (G == Gs::kHi) return dispatch_nch_mode<DT, Gs::kHi, MODE>(n, f);
+  if (G == 32) return dispatch_nch_mode<DT, 32, MODE>(n, f);
   return cudaErrorInvalidValue;
 }
 
@@ -87,8 +90,7 @@ struct ScoreConfig {
 template <int DT>
 ScoreConfig effective_config(int nch, int tuned_G, int tuned_mode) {
   auto fits = [&](int G, int mode) { return G > 0 && round_nch((nch + G - 1) / G, mode) <= 10; };
-  if ((tuned_G == Groups<DT>::kLo || tuned_G == Groups<DT>::G0 || tuned_G == Groups<DT>::kHi || tuned_G == 32) &&
-      fits(tuned_G, tuned_mode))
+  if (tuned_G > 0 && group_supported<DT>(tuned_G, tuned_mode) && fits(tuned_G, tuned_mode))
     return {tuned_G, tuned_mode};
   if (fits(Groups<DT>::G0, 0)) return {Groups<DT>::G0, 0};
   if (fits(Groups<DT>::kHi, 0)) return {Groups<DT>::kHi, 0};

@@ -324,23 +324,25 @@ struct FusedLaunch {
   }
 };
 
-template <int DT>
-cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, int RB, ScoreConfig cfg, cudaStream_t st) {
+// One gather mode's launchers; each (store type, mode) is instantiated in a translation unit
+// of its own (score_<type>_<kernel>_m<mode>.cu), the host code picks the mode at run time.
+template <int DT, int MODE>
+cudaError_t launch_score_mode(const ScoreArgs& a, dim3 grid, int RB, ScoreConfig cfg, cudaStream_t st) {
   ScoreLaunch f{a, grid, RB, cfg.carve_kb, st};
-  return dispatch_score<DT>(cfg.G, a.nch, cfg.mode, f);
+  return dispatch_score_mode<DT, MODE>(cfg.G, a.nch, f);
 }
 
-template <int DT>
-cudaError_t launch_fused_dt(const ScoreArgs& a, unsigned grid, int kappa, const ChunkPlan& plan, float* out_s,
-                            int32_t* out_id, ScoreConfig cfg, cudaStream_t st) {
+template <int DT, int MODE>
+cudaError_t launch_fused_mode(const ScoreArgs& a, unsigned grid, int kappa, const ChunkPlan& plan, float* out_s,
+                              int32_t* out_id, ScoreConfig cfg, cudaStream_t st) {
   FusedLaunch f{a, grid, kappa, plan, cfg.sched == 0 ? 1 : 0, out_s, out_id, cfg.carve_kb, st};
-  return dispatch_score<DT>(cfg.G, a.nch, cfg.mode == 2 ? 0 : cfg.mode, f);
+  return dispatch_score_mode<DT, MODE>(cfg.G, a.nch, f);
 }
 
-#define GLV_INSTANTIATE_SCORE_PLAIN(DT) \
-  template cudaError_t launch_score_dt<DT>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
-#define GLV_INSTANTIATE_SCORE_FUSED(DT)                                                                \
-  template cudaError_t launch_fused_dt<DT>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*, int32_t*, \
-                                           ScoreConfig, cudaStream_t);
+#define GLV_INSTANTIATE_SCORE_PLAIN(DT, MODE) \
+  template cudaError_t launch_score_mode<DT, MODE>(const ScoreArgs&, dim3, int, ScoreConfig, cudaStream_t);
+#define GLV_INSTANTIATE_SCORE_FUSED(DT, MODE)                                                              \
+  template cudaError_t launch_fused_mode<DT, MODE>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*, \
+                                                   int32_t*, ScoreConfig, cudaStream_t);
 
 }  // namespace glv

@@ -78,6 +78,23 @@ GLV_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64
       : "memory");
 }
 
+// 2-D TMA tile store (shared -> global) of the box at column x, row y; parts of the box
+// outside the tensor are not written.  Completion is tracked with the bulk async-group of
+// the issuing thread (tma_store_commit / tma_store_wait_read / tma_store_wait_all).
+GLV_DEV void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+GLV_DEV void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of all committed stores have been read (the buffer may be reused)
+GLV_DEV void tma_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// all committed stores are complete
+GLV_DEV void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// orders this thread's generic-proxy shared-memory writes before later async-proxy reads (TMA)
+GLV_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 GLV_DEV void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }

@@ -612,14 +612,16 @@ def test_every_score_configuration_matches_oracle(glv, dt_name):
 
 @pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("gi", [0, 1])
+@pytest.mark.parametrize("gi", [0, 1, 2])
 def test_fused_matches_separate_in_every_gather_mode(glv, dt_name, mode, gi):
     """Gather modes change only how rows travel; the scores (and so the selections) of the
     fused and the stand-alone (split) paths stay bit-identical for every group size."""
     dt = glv.DTYPES[dt_name]
+    G = glv.SCORE_GROUPS[dt][gi]
     try:
-        glv.glv_set_score_config(dt, glv.SCORE_GROUPS[dt][gi], mode)
+        glv.glv_set_score_config(dt, G, mode)
         test_score_topk_fused_matches_separate(glv, dt_name, 700, 100)
+        test_score_topk_fused_matches_separate(glv, dt_name, 700, 200)
     finally:
         glv.glv_set_score_config(dt, 0, 0)
 
