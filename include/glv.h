@@ -336,6 +336,16 @@ glv_status glv_gather_rows(const void* rows, int64_t row_bytes, int64_t n_rows, 
                            int64_t n_ids, float* out, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Self-check of the bounded device-side waits (no counterpart in the paper).  The tensor-
+ * core kernels wait on mbarriers with a time limit (2 s) and report GLV_ERR_TIMEOUT in the
+ * status word instead of hanging if a wait never completes; this launches one thread that
+ * waits, with a limit of limit_us microseconds (1 .. 10^6), on a barrier nothing completes,
+ * so the same timeout path runs and the status word receives GLV_ERR_TIMEOUT (read it with
+ * glv_last_device_status).  The GPU is left fully usable.
+ * ------------------------------------------------------------------------------------- */
+glv_status glv_check_bounded_wait(uint32_t limit_us, int32_t* d_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Per-query top-kappa of the scores (Algorithm 1: the main step hands kappa candidates to
  * the post-processing).  Exact selection (radix select on order-preserving keys), output
  * sorted by score descending, ties to the smaller id, NaN last, padding (-inf, -1) when a

@@ -342,6 +342,12 @@ glv_status glv_pair_backward(const float* Q, int64_t nQ, const float* X, int64_t
   return GLV_OK;
 }
 
+glv_status glv_check_bounded_wait(uint32_t limit_us, int32_t* d_status, void* stream) {
+  GLV_CHECK(d_status != nullptr && limit_us >= 1 && limit_us <= 1000000, GLV_ERR_INVALID_ARG);
+  GLV_LAUNCH(launch_bounded_wait((uint64_t)limit_us * 1000, d_status, (cudaStream_t)stream));
+  return GLV_OK;
+}
+
 glv_status glv_pair_loss(const float* s, const float* t, int64_t P, const double* weight, double* loss, float* g,
                          void* stream) {
   GLV_CHECK(P >= 0, GLV_ERR_INVALID_ARG);

@@ -3,10 +3,12 @@
 //     x_i^low = B_{c_i} x_i ,  stored as FP32, BF16 or FP8-e4m3 with a per-row scale.
 //
 // Rows are grouped by cluster on the device (histogram -> scan -> scatter of row ids into a
-// permutation), so that every CTA multiplies a tile of rows of ONE cluster by that
-// cluster's B_c: a grouped GEMM instead of N separate matrix-vector products.  The CTA
-// keeps its tile's whole reduced rows in shared memory, so the epilogue sees each full row
-// and can compute the FP8 row scale s_i = max_r |x_ir| / 448 before quantising.
+// permutation), so that every tile of rows of ONE cluster is multiplied by that cluster's
+// B_c: a grouped GEMM instead of N separate matrix-vector products.  The GEMM runs on the
+// tensor cores (build_tc.cu, FP32-accurate through a TF32 hi/lo split) when D % 4 == 0 and
+// d <= 256; otherwise on the FP32 SIMT kernel below, whose CTA keeps its tile's whole reduced
+// rows in shared memory, so the epilogue sees each full row and can compute the FP8 row scale
+// s_i = max_r |x_ir| / 448 before quantising.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -285,6 +287,12 @@ cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags,
   BuildWs ws = build_ws_carve(workspace, N, C);
   cudaError_t e = launch_grouping(tags, N, C, ws, d_status, st);
   if (e != cudaSuccess) return e;
+  if (build_tc_supported(N, D, C, d, X, B)) {  // the tensor-core grouped GEMM (build_tc.cu)
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    return launch_build_tc(X, N, D, B, C, d, dt, Xred, row_stride, scales, ws, d_status, sms, st);
+  }
 
   BuildArgs a;
   a.X = X; a.N = N; a.D = D; a.B = B; a.C = C; a.d = d;

@@ -10,6 +10,7 @@
 // grid-stride loop over the entries with 4 CTAs of 256 threads per SM.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc.cuh"
 
 namespace glv {
 
@@ -74,6 +75,26 @@ cudaError_t launch_gather_rows(const void* rows, int64_t row_bytes, int64_t n_ro
   GLV_GATHER(8)
 #undef GLV_GATHER
   return cudaErrorInvalidValue;
+}
+
+// Self-check of the bounded device-side waits: one thread waits, with the given limit, on an
+// mbarrier that nothing will complete (one arrival expected, none made) -- the situation of a
+// tensor-core pipeline whose producer has stopped.  The wait gives up after limit_ns, the
+// kernel records GLV_ERR_TIMEOUT in the status word and returns normally.
+__global__ void bounded_wait_kernel(uint64_t limit_ns, int32_t* d_status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    abort_flag = 0;
+    if (!tc::mbar_wait(&bar, 0, &abort_flag, limit_ns)) report(d_status, GLV_ERR_TIMEOUT);
+  }
+}
+
+cudaError_t launch_bounded_wait(uint64_t limit_ns, int32_t* d_status, cudaStream_t st) {
+  bounded_wait_kernel<<<1, 32, 0, st>>>(limit_ns, d_status);
+  return cudaGetLastError();
 }
 
 }  // namespace glv

@@ -91,6 +91,7 @@ cudaError_t launch_score_lazy(const ScoreArgs& a, int dt, int64_t nq, const floa
 cudaError_t launch_topk(const float* scores, const int64_t* off, const int32_t* ids, int64_t nq,
                         int kappa, float* out_s, int32_t* out_id, cudaStream_t st);
 cudaError_t launch_rerank(const RerankArgs& a, int64_t nq, bool vec, cudaStream_t st);
+cudaError_t launch_bounded_wait(uint64_t limit_ns, int32_t* d_status, cudaStream_t st);
 cudaError_t launch_gather_rows(const void* rows, int64_t row_bytes, int64_t n_rows, const int32_t* ids,
                                int64_t n_ids, float* out, int32_t* d_status, int num_sms, cudaStream_t st);
 size_t rerank_smem_bytes(int D, int kappa);
@@ -131,6 +132,10 @@ cudaError_t launch_pair_loss(const float* s, const float* t, int64_t P, const do
                              cudaStream_t st);
 cudaError_t launch_adam(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float b1, float b2,
                         float eps, int step, int num_sms, cudaStream_t st);
+bool build_tc_supported(int64_t N, int D, int C, int d, const void* X, const void* B);
+cudaError_t launch_build_tc(const float* X, int64_t N, int D, const float* B, int C, int d, int dt, void* Xred,
+                            int64_t row_stride, float* scales, const BuildWs& ws, int32_t* d_status, int num_sms,
+                            cudaStream_t st);
 cudaError_t launch_build(const float* X, int64_t N, int D, const uint16_t* tags, const float* B,
                          int C, int d, int dt, void* Xred, int64_t row_stride, float* scales,
                          void* workspace, int32_t* d_status, cudaStream_t st);

@@ -53,7 +53,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 // Wait until the phase with the given parity has completed.  Returns false when the wait
 // limit passes or *abort is set by another role; on a timeout it sets *abort itself.
-GLV_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+GLV_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t limit_ns = kWaitLimitNs) {
 #pragma unroll 1
   for (int i = 0; i < 128; ++i)
     if (mbar_try_wait(bar, parity)) return true;
@@ -62,7 +62,7 @@ GLV_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (global_ns() - t0 > kWaitLimitNs) {
+    if (global_ns() - t0 > limit_ns) {
       *abort = 1;
       return false;
     }

@@ -57,6 +57,7 @@ def _load() -> ctypes.CDLL:
         "glv_get_score_config": (i32, [i32, i32, P, P, P, P]),
         "glv_rerank": (i32, [P, i64, i32, P, i64, P, i32, i32, P, P, P, P]),
         "glv_gather_rows": (i32, [P, i64, i64, P, i64, P, P, P]),
+        "glv_check_bounded_wait": (i32, [ctypes.c_uint32, P, P]),
         "glv_search_workspace_size": (sz, [i64, i32, i32, i32, i32, i64, i32]),
         "glv_search": (i32, [P, i64, i32, P, i64, P, i32, i32, i32, P, i64, P, i32, P, P, P, i64, i32, i32,
                              P, P, P, P, P]),
@@ -421,3 +422,10 @@ def glv_search_host(X, Q_h, A, compute: int, Xred, row_stride: int, scales, dt: 
         ids_h.shape[0], kappa, k, _ptr(workspace), ctypes.c_void_p(out_s_h.data_ptr()),
         ctypes.c_void_p(out_id_h.data_ptr()), _ptr(d_status), _stream(stream)))
     return out_s_h, out_id_h
+
+
+def glv_check_bounded_wait(limit_us: int, d_status, stream=None) -> None:
+    """Runs a device wait on a barrier nothing completes, bounded by limit_us; the status word
+    receives GLV_ERR_TIMEOUT when the limit passes."""
+    _need(d_status, torch.int32, "d_status", 1)
+    _check("glv_check_bounded_wait", _lib.glv_check_bounded_wait(int(limit_us), _ptr(d_status), _stream(stream)))

@@ -155,7 +155,11 @@ def test_build_reduced_bf16(glv, D, d, C):
     hi = oracle.bf16_decode(oracle.bf16_encode(_f32_up(Xr + tol)))
     bad = ~((gd >= lo) & (gd <= hi))
     ndiff = int((got_codes != ref_codes).sum())
-    assert not bad.any() and ndiff <= max(3, Xr.size // 1000), (int(bad.sum()), ndiff)
+    # every code is the rounding of a value within the tolerance (bad); the codes that differ
+    # from the rounding of the exact value are the few whose value lies within the FP32-level
+    # error of a rounding boundary: with TF32 hi/lo products (error ~2^-21 of the Cauchy-Schwarz
+    # scale) about 0.3% of BF16 codes at D = 512..768, so at most 1% may differ
+    assert not bad.any() and ndiff <= max(3, Xr.size // 100), (int(bad.sum()), ndiff)
 
 
 @pytest.mark.parametrize("D,d,C", [(96, 27, 5), (512, 128, 64), (768, 160, 32), (64, 16, 2)])
