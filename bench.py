@@ -772,7 +772,7 @@ def measure_workload(name, args, *, dev, rank, world, local, flush, peaks, store
                                 f"restricted to the {len(sp['uniq'])} rows they touch")
         if args.score_error and headline:
             out["score_error_vs_fp64_oracle"] = score_error_block(glv, idx, w, sp, qsel, stores)
-        if name == "precision-10M-d128" or (headline and args.kappa_sweep not in ("auto", "none")):
+        if args.kappa_sweep != "none" and (name == "precision-10M-d128" or (headline and args.kappa_sweep != "auto")):
             kaps = KAPPA_SWEEP if args.kappa_sweep in ("auto",) else [int(x) for x in args.kappa_sweep.split(",")]
             out["kappa_sweep"], out["equal_recall"] = kappa_sweep_block(glv, idx, w, stores, kaps, sp, red, exact,
                                                                         qsel, counts, args, flush, world)
