@@ -725,7 +725,7 @@ def measure_workload(name, args, *, dev, rank, world, local, flush, peaks, store
            "stores": {st: {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernels_ms": r["kernels_ms"],
                            "roofline": roof[st]} for st, r in res.items()}}
     out["_results"] = res
-    out["_launches_per_step"] = {st: 5 + (1 if tuned[st]["schedule"] == 1 else 0) for st in stores}
+    out["_launches_per_step"] = {st: 5 + (tuned[st]["schedule"] & 1) for st in stores}
 
     if name == "batching-2M-d192" or (headline and (args.graph or args.per_query)):
         out["batching"] = batching_block(glv, idx[stores[0]], w, args, flush, world, dev)

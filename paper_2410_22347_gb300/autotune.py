@@ -24,7 +24,7 @@ CACHE = os.environ.get("GLV_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"
 
 def _key(dt: int, d: int, C: int, mean_len: float) -> str:
     name = torch.cuda.get_device_name()
-    return f"v4|{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
+    return f"v5|{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
 
 
 def _load_cache() -> dict:
@@ -47,11 +47,14 @@ def _save_cache(c: dict) -> None:
 
 
 def configurations(dt: int):
-    # the fused call gathers into registers (modes 0 and 1; it maps the bulk mode to 0)
-    for G in glv.SCORE_GROUPS[dt]:
-        for mode in (0, 1):
-            for carve in glv.SCORE_CARVEOUTS:
-                for sched in glv.SCORE_SCHEDULES:
+    # the fused call gathers into registers (modes 0 and 1; it maps the bulk mode to 0); the
+    # wide schedules (bit 1) exist for mode 0 and the two smaller lane counts
+    for sched in glv.SCORE_SCHEDULES:
+        for G in glv.SCORE_GROUPS[dt]:
+            for mode in (0, 1):
+                if (sched & 2) and (mode != 0 or G not in glv.SCORE_GROUPS[dt][:2]):
+                    continue
+                for carve in glv.SCORE_CARVEOUTS:
                     yield G, mode, carve, sched
 
 

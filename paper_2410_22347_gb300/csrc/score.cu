@@ -21,7 +21,9 @@ namespace glv {
   extern template cudaError_t launch_fused_mode<DT, 0>(const ScoreArgs&, unsigned, int, const ChunkPlan&,       \
                                                        float*, int32_t*, ScoreConfig, cudaStream_t);            \
   extern template cudaError_t launch_fused_mode<DT, 1>(const ScoreArgs&, unsigned, int, const ChunkPlan&,       \
-                                                       float*, int32_t*, ScoreConfig, cudaStream_t);
+                                                       float*, int32_t*, ScoreConfig, cudaStream_t);        \
+  extern template cudaError_t launch_fused_wide<DT>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*,  \
+                                                    int32_t*, ScoreConfig, cudaStream_t);
 GLV_EXTERN_MODES(GLV_F32)
 GLV_EXTERN_MODES(GLV_BF16)
 GLV_EXTERN_MODES(GLV_FP8_E4M3)
@@ -38,6 +40,7 @@ static cudaError_t launch_score_dt(const ScoreArgs& a, dim3 grid, int RB, ScoreC
 template <int DT>
 static cudaError_t launch_fused_dt(const ScoreArgs& a, unsigned grid, int kappa, const ChunkPlan& plan, float* out_s,
                                    int32_t* out_id, ScoreConfig cfg, cudaStream_t st) {
+  if (cfg.sched & 2) return launch_fused_wide<DT>(a, grid, kappa, plan, out_s, out_id, cfg, st);
   switch (cfg.mode) {
     case 1: return launch_fused_mode<DT, 1>(a, grid, kappa, plan, out_s, out_id, cfg, st);
     default: return launch_fused_mode<DT, 0>(a, grid, kappa, plan, out_s, out_id, cfg, st);  // bulk (2) -> 0
@@ -50,7 +53,7 @@ static std::mutex g_cfg_mu;
 static ScoreConfig g_cfg[3] = {{0, 0, 0, 1}, {0, 0, 0, 1}, {0, 0, 0, 1}};  // G = 0: library default
 
 bool set_score_config(int dt, int G, int mode, int carve_kb, int sched) {
-  if (dt < 0 || dt > 2 || mode < 0 || mode > 2 || sched < 0 || sched > 1) return false;
+  if (dt < 0 || dt > 2 || mode < 0 || mode > 2 || sched < 0 || sched > 3) return false;
   const bool ok = (G == 0) || G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32;
   if (!ok) return false;
   if (carve_kb != 0 && (carve_kb < 16 || carve_kb > 256)) return false;
@@ -82,6 +85,14 @@ ScoreConfig resolve_config(int dt, int nch) {
   }
   c.carve_kb = t.carve_kb;
   c.sched = t.sched;
+  // the wide fused kernel: register loads with one of the two smaller group sizes
+  bool wide_ok = false;
+  switch (dt) {
+    case GLV_F32: wide_ok = wide_group_supported<GLV_F32>(c.G); break;
+    case GLV_BF16: wide_ok = wide_group_supported<GLV_BF16>(c.G); break;
+    default: wide_ok = wide_group_supported<GLV_FP8_E4M3>(c.G); break;
+  }
+  if ((c.sched & 2) && (!wide_ok || c.mode != 0)) c.sched &= 1;
   return c;
 }
 
@@ -254,16 +265,21 @@ cudaError_t launch_score_topk(const ScoreArgs& a0, int dt, int64_t nq, int64_t n
   a.qstride = qstride_of(a.d, dt);
   a.sbs = qp_sbs(a.nch, dt);
   a.splits = 1;
-  const ScoreConfig cfg = resolve_config(dt, a.nch);
+  ScoreConfig cfg = resolve_config(dt, a.nch);
+  // wide CTAs keep twice the keys on chip; where that does not fit, the 256-thread kernel runs
+  if ((cfg.sched & 2) &&
+      score_smem(a.C, a.qstride, true, 0, 0, a.nch, kappa, fused_cache(kWideThreads)).total() > kScoreSmemLimit)
+    cfg.sched &= 1;
   const ChunkPlan plan = topk_plan_layout(plan_ws, nq);
-  unsigned grid = (unsigned)nq;  // schedule 0: one CTA per query
-  if (cfg.sched != 0) {
+  unsigned grid = (unsigned)nq;  // one CTA per query
+  if (cfg.sched & 1) {
     cudaError_t e = launch_plan_chunks(a.off, nq, n_cand, plan_ws, a.d_status, st);
     if (e != cudaSuccess) return e;
-    // persistent CTAs claim items dynamically: 8 per SM covers any occupancy, the extra ones
-    // find no item left and exit
+    // persistent CTAs claim items dynamically: as many as the SM's thread slots allow (2048
+    // threads) covers any occupancy, the extra ones find no item left and exit
     const int64_t items = max_items(nq, n_cand);
-    grid = (unsigned)(items < (int64_t)num_sms * 8 ? items : (int64_t)num_sms * 8);
+    const int64_t per_sm = (cfg.sched & 2) ? 2048 / kWideThreads : 2048 / kScoreThreads;
+    grid = (unsigned)(items < (int64_t)num_sms * per_sm ? items : (int64_t)num_sms * per_sm);
   }
   switch (dt) {
     case GLV_F32: return launch_fused_dt<GLV_F32>(a, grid, kappa, plan, out_s, out_id, cfg, st);

@@ -74,6 +74,22 @@ cudaError_t dispatch_score_mode(int G, int nch, F& f) {
   return cudaErrorInvalidValue;
 }
 
+// The wide fused kernel (512 threads) is instantiated for the two smaller group sizes of a
+// store type, register loads only.
+template <int DT>
+inline bool wide_group_supported(int G) {
+  return G == Groups<DT>::kLo || G == Groups<DT>::G0;
+}
+
+template <int DT, class F>
+cudaError_t dispatch_score_wide(int G, int nch, F& f) {
+  using Gs = Groups<DT>;
+  const int n = round_nch((nch + G - 1) / G, 0);
+  if (G == Gs::kLo) return dispatch_nch_mode<DT, Gs::kLo, 0>(n, f);
+  if (G == Gs::G0) return dispatch_nch_mode<DT, Gs::G0, 0>(n, f);
+  return cudaErrorInvalidValue;
+}
+
 // Effective configuration for a row of nch chunks: the tuned choice if it can serve the
 // row, else the default group (or 32 lanes for wide rows) with register loads.
 // Lanes per candidate, gather mode, the shared-memory carveout cap in KB (0 = the driver's
@@ -84,7 +100,8 @@ struct ScoreConfig {
   int G;
   int mode;
   int carve_kb = 0;
-  int sched = 1;  // fused call: 1 = planned work items (chunked long lists), 0 = one CTA per query
+  int sched = 1;  // fused call, bit 0: planned work items (chunked long lists), else one CTA per
+                  // query; bit 1: wide CTAs (512 threads, register loads)
 };
 
 template <int DT>

@@ -12,9 +12,13 @@
 
 namespace glv {
 
-constexpr int kFusedCache = 2048;  // list entries kept as keys in shared memory
 constexpr int kBulkSlots = 2;      // ring slots per warp (bulk gather)
 constexpr int kScoreThreads = 256;
+constexpr int kWideThreads = 512;  // fused kernel, wide schedule: twice the warps per staged query
+// List entries the fused kernel keeps as keys in shared memory: kWarpThrKeys per thread, the
+// most the per-warp threshold selection takes (2048 for 256 threads, 4096 for 512).
+constexpr int fused_cache(int threads) { return kWarpThrKeys * threads; }
+constexpr int kFusedCache = fused_cache(kScoreThreads);
 
 // Shared-memory carve-up shared by host and device: [projected query | keys | rings | bars].
 struct ScoreSmem {
@@ -22,14 +26,14 @@ struct ScoreSmem {
   __host__ __device__ size_t total() const { return qs_bytes + keys_bytes + ring_bytes + bar_bytes; }
 };
 
-// keys_bytes (fused only): kFusedCache cached keys, then the kappa selected keys and ids,
+// keys_bytes (fused only): `cache` cached keys, then the kappa selected keys and ids,
 // rounded to 128 bytes so the rings stay aligned.
 __host__ __device__ inline ScoreSmem score_smem(int C, int qstride, bool fused, int mode, int RB, int nch,
-                                                int kappa = 0) {
+                                                int kappa = 0, int cache = kFusedCache) {
   ScoreSmem m;
   // the C rows of projected views, then C per-cluster factors (used by FP8 rows)
   m.qs_bytes = (((size_t)C * (qstride + 1) * sizeof(float)) + 127) & ~size_t(127);
-  m.keys_bytes = fused ? (((size_t)kFusedCache * sizeof(uint32_t) + (size_t)kappa * 8) + 127) & ~size_t(127) : 0;
+  m.keys_bytes = fused ? (((size_t)cache * sizeof(uint32_t) + (size_t)kappa * 8) + 127) & ~size_t(127) : 0;
   const int warps = kScoreThreads / 32;
   m.ring_bytes = mode == 2 ? (size_t)warps * kBulkSlots * RB * nch * 16 : 0;
   m.bar_bytes = mode == 2 ? (size_t)warps * kBulkSlots * sizeof(uint64_t) : 0;
@@ -54,6 +58,12 @@ constexpr int fused_min_blocks_regs(int n) { return n <= 3 ? GLV_FUSED_MINB : n 
 // FP8 decode costs about two chunks' worth of registers more.
 constexpr int fused_min_blocks(int dt, int mode, int nch) {
   return mode == 2 ? 1 : mode == 1 ? 3 : fused_min_blocks_regs(nch + (dt == GLV_FP8_E4M3 ? 2 : 0));
+}
+// The same register budget per thread for CTAs of `threads` threads.
+constexpr int fused_min_blocks_t(int dt, int mode, int nch, int threads) {
+  return fused_min_blocks(dt, mode, nch) * kScoreThreads / threads > 0
+             ? fused_min_blocks(dt, mode, nch) * kScoreThreads / threads
+             : 1;
 }
 
 template <int DT, int G, int NCH, int MODE, class Sink>
@@ -113,16 +123,20 @@ __global__ void __launch_bounds__(kScoreThreads) score_kernel(const ScoreArgs a,
 
 // Gather-score and top-kappa, persistent: each CTA claims work items (a whole candidate list,
 // or a chunk of at most kChunk candidates of a long one) from the plan until none is left.
-// Scores stay on chip as order-preserving keys in shared memory and the radix selection runs
-// there; an item longer than the key cache spills its scores to the caller's scratch.  A chunk
+// Scores stay on chip as order-preserving keys in shared memory and the selection runs
+// there; an item longer than the key cache (fused_cache(TPB) keys) spills its scores to the
+// caller's scratch.  TPB = 256 or 512 threads: the wide CTA spreads one staged query over
+// twice the warps (more row loads in flight per SM for the same shared memory) and keeps
+// twice the keys on chip.  A chunk
 // of a long list writes its own top-kappa at the start of its part of the scratch (scores then
 // ids); the CTA that finishes a query's last chunk (a fenced per-query counter; nothing waits)
 // selects the query's top-kappa from the chunks' lists, which contain it: a candidate outside
 // its chunk's top-kappa has kappa candidates of that chunk ranked before it.
-template <int DT, int G, int NCH, int MODE>
-__global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH))
+template <int DT, int G, int NCH, int MODE, int TPB>
+__global__ void __launch_bounds__(TPB, fused_min_blocks_t(DT, MODE, NCH, TPB))
     score_topk_kernel(const ScoreArgs a, int kappa, ChunkPlan plan, int direct, float* out_s, int32_t* out_id) {
   static_assert(MODE != 2, "the fused kernel gathers rows into registers");
+  constexpr int kCache = fused_cache(TPB);
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ TopkSmem S;
   // work items, double-buffered: slot cur holds the current item, thread 0 fills the other
@@ -130,14 +144,14 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
   __shared__ __align__(16) ItemRec s_rec[2];
   __shared__ int s_valid[2], s_last, s_claimed, s_items;  // s_claimed: next item, claimed ahead
   __shared__ int64_t s_staged;
-  const ScoreSmem L = score_smem(a.C, a.qstride, true, MODE, 0, a.nch, kappa);
+  const ScoreSmem L = score_smem(a.C, a.qstride, true, MODE, 0, a.nch, kappa, kCache);
   float* qs = reinterpret_cast<float*>(smem);
   uint32_t* kc = reinterpret_cast<uint32_t*>(smem + L.qs_bytes);
   if (threadIdx.x == 0) {
-    S.sel_key = kc + kFusedCache;
-    S.sel_id = reinterpret_cast<int32_t*>(kc + kFusedCache + kappa);
+    S.sel_key = kc + kCache;
+    S.sel_id = reinterpret_cast<int32_t*>(kc + kCache + kappa);
     S.region = kc;
-    S.region_words = kFusedCache;
+    S.region_words = kCache;
     s_staged = -1;
     if (direct) {  // one CTA per query, no plan: the query's whole list is the only item
       const int64_t q = blockIdx.x, p0 = a.off[q];
@@ -181,7 +195,7 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
     __syncthreads();
     if (threadIdx.x == 0) s_staged = j;
     const int64_t b0 = s_rec[cur].b0, b1 = b0 + s_rec[cur].len;
-    if (b1 - b0 <= kFusedCache) {
+    if (b1 - b0 <= kCache) {
       auto sink = [kc, b0](int64_t p, float s) { kc[p - b0] = score_key(s); };
       score_range<DT, G, NCH, MODE == 1>(a, qs, b0, b1, sink);
     } else {
@@ -217,7 +231,7 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
     // re-read the item after the barrier (nothing of it stays live across the gather)
     const int nchunks = s_rec[cur].nchunks;
     const int64_t jj = s_rec[cur].q, c0 = s_rec[cur].b0, lc = s_rec[cur].len;
-    const bool in_kc = lc <= kFusedCache;
+    const bool in_kc = lc <= kCache;
     const float* sj = scores + c0;
     const int32_t* ij = a.ids + c0;
     if (nchunks == 1) {
@@ -242,7 +256,7 @@ __global__ void __launch_bounds__(kScoreThreads, fused_min_blocks(DT, MODE, NCH)
         const float* base = scores + a.off[jj];
         const int64_t kap = kappa;
         auto ent = [base, kap](int64_t e) { return base + (e / kap) * kChunk + (e % kap); };
-        const bool mc = M <= kFusedCache;
+        const bool mc = M <= kCache;
         if (mc)
           for (int64_t e = threadIdx.x; e < M; e += blockDim.x) kc[e] = score_key(__ldcg(ent(e)));
         __syncthreads();
@@ -297,6 +311,7 @@ struct ScoreLaunch {
   }
 };
 
+template <int TPB>
 struct FusedLaunch {
   const ScoreArgs& a;
   unsigned grid;
@@ -312,13 +327,13 @@ struct FusedLaunch {
     if constexpr (MODE == 2) {
       return cudaErrorInvalidValue;  // the launcher maps the bulk gather to register loads
     } else {
-      auto k = score_topk_kernel<DT, G, NCH, MODE>;
-      const size_t smem = score_smem(a.C, a.qstride, true, MODE, 0, a.nch, kappa).total();
+      auto k = score_topk_kernel<DT, G, NCH, MODE, TPB>;
+      const size_t smem = score_smem(a.C, a.qstride, true, MODE, 0, a.nch, kappa, fused_cache(TPB)).total();
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       e = apply_carveout(reinterpret_cast<const void*>(k), smem, carve_kb);
       if (e != cudaSuccess) return e;
-      k<<<grid, kScoreThreads, smem, st>>>(a, kappa, plan, direct, out_s, out_id);
+      k<<<grid, TPB, smem, st>>>(a, kappa, plan, direct, out_s, out_id);
       return cudaGetLastError();
     }
   }
@@ -335,8 +350,16 @@ cudaError_t launch_score_mode(const ScoreArgs& a, dim3 grid, int RB, ScoreConfig
 template <int DT, int MODE>
 cudaError_t launch_fused_mode(const ScoreArgs& a, unsigned grid, int kappa, const ChunkPlan& plan, float* out_s,
                               int32_t* out_id, ScoreConfig cfg, cudaStream_t st) {
-  FusedLaunch f{a, grid, kappa, plan, cfg.sched == 0 ? 1 : 0, out_s, out_id, cfg.carve_kb, st};
+  FusedLaunch<kScoreThreads> f{a, grid, kappa, plan, (cfg.sched & 1) ? 0 : 1, out_s, out_id, cfg.carve_kb, st};
   return dispatch_score_mode<DT, MODE>(cfg.G, a.nch, f);
+}
+
+// The wide schedule (kWideThreads threads, register gather, the two smaller group sizes).
+template <int DT>
+cudaError_t launch_fused_wide(const ScoreArgs& a, unsigned grid, int kappa, const ChunkPlan& plan, float* out_s,
+                              int32_t* out_id, ScoreConfig cfg, cudaStream_t st) {
+  FusedLaunch<kWideThreads> f{a, grid, kappa, plan, (cfg.sched & 1) ? 0 : 1, out_s, out_id, cfg.carve_kb, st};
+  return dispatch_score_wide<DT>(cfg.G, a.nch, f);
 }
 
 #define GLV_INSTANTIATE_SCORE_PLAIN(DT, MODE) \
@@ -344,5 +367,8 @@ cudaError_t launch_fused_mode(const ScoreArgs& a, unsigned grid, int kappa, cons
 #define GLV_INSTANTIATE_SCORE_FUSED(DT, MODE)                                                              \
   template cudaError_t launch_fused_mode<DT, MODE>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*, \
                                                    int32_t*, ScoreConfig, cudaStream_t);
+#define GLV_INSTANTIATE_SCORE_WIDE(DT)                                                                  \
+  template cudaError_t launch_fused_wide<DT>(const ScoreArgs&, unsigned, int, const ChunkPlan&, float*, \
+                                             int32_t*, ScoreConfig, cudaStream_t);
 
 }  // namespace glv

@@ -18,8 +18,9 @@
 //
 // Lists whose keys are cached in the region with at most 8 per thread skip the block-wide
 // radix passes: a per-warp threshold (warp_threshold_filter) that provably leaves at least
-// kappa keys, one packing pass, and a rank count over the (typically 1.5 kappa, at most 256)
-// survivors, which writes the top kappa already sorted.  Wide tie groups take the radix path.
+// kappa keys, one packing pass, and a rank count over the (typically 1.5 kappa, at most one
+// per thread) survivors, which writes the top kappa already sorted.  Wide tie groups take the
+// radix path.
 //
 // The kappa winners are sorted by (key desc, id asc).  After a filtered selection, up to 256
 // of them go through a bitonic network across the CTA's threads on the packed 64-bit value
@@ -226,29 +227,31 @@ GLV_DEV void sort8_desc(uint32_t (&v)[8]) {
   }
 }
 
-// Keys cached in the region, at most kWarpThrKeys per thread (256 threads): a threshold T that
-// at least kappa of the L keys reach, found with one barrier.  Each warp pops the
-// r = ceil(kappa / 8) largest of its own keys (every lane's keys sorted in registers, one
-// warp max-reduction per pop), and T is the smallest of the eight warps' r-th largest keys,
-// so each warp holds r keys >= T and at least 8 r >= kappa list keys reach T (on random
-// scores about 1.5 kappa do).  One pass then packs every key >= T with its id
+// Keys cached in the region, at most kWarpThrKeys per thread: a threshold T that at least
+// kappa of the L keys reach, found with one barrier.  With W warps, each warp pops the
+// r = ceil(kappa / W) largest of its own keys (every lane's keys sorted in registers, one
+// warp max-reduction per pop), and T is the smallest of the W warps' r-th largest keys, so
+// each warp holds r keys >= T and at least W r >= kappa list keys reach T (on random scores
+// about 1.5 kappa do).  One pass then packs every key >= T with its id
 // (key << 32 | id_rank(id)) into the region as 64-bit values and returns how many there are
 // (they hold the top kappa, ties included).  When that is more than one per thread (a wide
 // tie group), the keys are put back in the region and -1 is returned, for the radix path.
-// S.thr (all ones) and S.fill (0) are set by the caller before its barrier.
+// The region holds at least 2 blockDim.x words.  S.thr (all ones) and S.fill (0) are set by
+// the caller before its barrier.
 constexpr int kWarpThrKeys = 8;
 
 template <class KeyOf, class IdOf>
 GLV_DEV int warp_threshold_filter(TopkSmem& S, int L, int kappa, KeyOf key_of, IdOf id_of) {
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x, lane = t & 31, nt = blockDim.x;
   uint32_t v[kWarpThrKeys];
 #pragma unroll
   for (int i = 0; i < kWarpThrKeys; ++i) {
-    const int p = t + i * kTopkThreads;
+    const int p = t + i * nt;
     v[i] = p < L ? key_of(p) : 0u;
   }
   sort8_desc(v);
-  const int r = (kappa + 7) / 8;
+  const int nw = nt >> 5;
+  const int r = (kappa + nw - 1) / nw;
   uint32_t tw = 0;
   for (int s = 0; s < r; ++s) {
     const uint32_t m = __reduce_max_sync(0xffffffffu, v[0]);
@@ -263,7 +266,7 @@ GLV_DEV int warp_threshold_filter(TopkSmem& S, int L, int kappa, KeyOf key_of, I
   uint32_t k[kWarpThrKeys];
 #pragma unroll
   for (int i = 0; i < kWarpThrKeys; ++i) {
-    const int p = t + i * kTopkThreads;
+    const int p = t + i * nt;
     k[i] = p < L ? key_of(p) : 0u;
   }
   __syncthreads();  // T is final, and every key is in registers: the region is free
@@ -271,20 +274,20 @@ GLV_DEV int warp_threshold_filter(TopkSmem& S, int L, int kappa, KeyOf key_of, I
   uint32_t tot = 0;
 #pragma unroll
   for (int i = 0; i < kWarpThrKeys; ++i)
-    tot += __popc(__ballot_sync(0xffffffffu, t + i * kTopkThreads < L && k[i] >= T));
+    tot += __popc(__ballot_sync(0xffffffffu, t + i * nt < L && k[i] >= T));
   uint32_t base = 0;
   if (lane == 0 && tot) base = atomicAdd(&S.fill, tot);
   base = __shfl_sync(0xffffffffu, base, 0);
   const unsigned lt = (1u << lane) - 1u;
-  const uint32_t cap = kTopkThreads;
+  const uint32_t cap = (uint32_t)nt;
   uint64_t* xs = reinterpret_cast<uint64_t*>(S.region);
 #pragma unroll
   for (int i = 0; i < kWarpThrKeys; ++i) {
-    const bool pass = t + i * kTopkThreads < L && k[i] >= T;
+    const bool pass = t + i * nt < L && k[i] >= T;
     const unsigned bal = __ballot_sync(0xffffffffu, pass);
     if (pass) {
       const uint32_t slot = base + __popc(bal & lt);
-      if (slot < cap) xs[slot] = ((uint64_t)k[i] << 32) | id_rank(id_of(t + i * kTopkThreads));
+      if (slot < cap) xs[slot] = ((uint64_t)k[i] << 32) | id_rank(id_of(t + i * nt));
     }
     base += __popc(bal);
   }
@@ -293,7 +296,7 @@ GLV_DEV int warp_threshold_filter(TopkSmem& S, int L, int kappa, KeyOf key_of, I
   if (n <= cap) return (int)n;
 #pragma unroll
   for (int i = 0; i < kWarpThrKeys; ++i) {
-    const int p = t + i * kTopkThreads;
+    const int p = t + i * nt;
     if (p < L) S.region[p] = k[i];
   }
   __syncthreads();
@@ -421,8 +424,8 @@ GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, bool in_region, KeyO
     if (threadIdx.x == 0) S.count = (uint32_t)L;
   } else {
     bool done = false;
-    if (in_region && L <= (int64_t)kWarpThrKeys * kTopkThreads && blockDim.x == kTopkThreads &&
-        kappa <= kFilterMaxKappa && S.region_words >= 512) {
+    if (in_region && L <= (int64_t)kWarpThrKeys * blockDim.x && kappa <= kFilterMaxKappa &&
+        S.region_words >= 2 * (int)blockDim.x) {
       const int n = warp_threshold_filter(S, (int)L, kappa, key_of, id_of);
       const uint64_t* xs = reinterpret_cast<const uint64_t*>(S.region);
       if (n >= 0) {

@@ -298,10 +298,11 @@ GATHER_MODES = (0, 1, 2)  # registers, registers pipelined, bulk copies into sha
 
 # shared-memory carveout caps the autotuner tries, KB (0 = the driver's choice; 164 leaves
 # about 92 KB of the SM's 256 KB to L1 for the rows in flight)
-SCORE_CARVEOUTS = (0, 164)
+SCORE_CARVEOUTS = (0, 132, 164)
 
-# fused-call schedules: 1 = planned work items (long lists cut into chunks), 0 = one CTA per query
-SCORE_SCHEDULES = (1, 0)
+# fused-call schedules, bit 0: planned work items (long lists cut into chunks), else one CTA per
+# query; bit 1: wide CTAs (512 threads, twice the keys on chip)
+SCORE_SCHEDULES = (1, 0, 3, 2)
 
 
 def glv_set_score_config(dt: int, lanes_per_candidate: int, gather_mode: int, smem_carveout_kb: int = 0,

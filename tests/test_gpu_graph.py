@@ -33,7 +33,7 @@ def _inputs(synth, nq, N, D, lengths, seed, dev):
     return Q, off, ids
 
 
-@pytest.mark.parametrize("schedule", [1, 0])
+@pytest.mark.parametrize("schedule", [1, 0, 3])
 def test_captured_search_replays_match_eager_launches(glv, schedule):
     from paper_2410_22347_gb300 import synth
     dev = torch.device("cuda:0")

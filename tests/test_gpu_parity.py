@@ -488,6 +488,7 @@ def test_score_topk_fused_matches_separate(glv, dt_name, nq, kappa):
     # into 2 and 4 work items (8192 and 16500 candidates) whose chunk lists are merged
     lens[:7] = [0, 1, kappa, 2048, 2049, 5000, 16500]
     lens[10] = 8192
+    lens[11:13] = [4096, 4097]  # the key-cache edge of the wide (512-thread) schedule
     lists = _ragged_lists(rng, nq, len(X), lens)
     lists[7] = np.concatenate([lists[7][:10], [len(X) + 5]])  # a bad id
     # bad ids score -inf and tie there: ties go to the smaller (signed) id, so negative ids
@@ -640,7 +641,11 @@ def test_score_config_roundtrip(glv):
         glv.glv_set_score_config(glv.GLV_BF16, 4, 2, 164, 0)
         assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (4, 2, 164, 0)
         with pytest.raises(glv.GlvError):
-            glv.glv_set_score_config(glv.GLV_BF16, 4, 0, 0, 2)
+            glv.glv_set_score_config(glv.GLV_BF16, 4, 0, 0, 4)
+        glv.glv_set_score_config(glv.GLV_BF16, 8, 0, 132, 2)
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, 0, 132, 2)
+        glv.glv_set_score_config(glv.GLV_BF16, 8, 1, 0, 3)  # no wide kernel with pipelined loads
+        assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, 1, 0, 1)
         with pytest.raises(glv.GlvError):
             glv.glv_set_score_config(glv.GLV_BF16, 3, 0)
         with pytest.raises(glv.GlvError):
@@ -659,9 +664,27 @@ def test_carveout_and_schedule_change_no_result(glv, dt_name, kappa):
     dt = glv.DTYPES[dt_name]
     try:
         for carve in (0, 164):
-            for sched in (1, 0):
+            for sched in (1, 0, 3, 2):
                 glv.glv_set_score_config(dt, 0, 0, carve, sched)
                 test_score_topk_fused_matches_separate(glv, dt_name, 700, kappa)
+    finally:
+        glv.glv_set_score_config(dt, 0, 0)
+
+
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("gi", [0, 1])
+@pytest.mark.parametrize("sched", [3, 2])
+def test_wide_schedule_matches_separate(glv, dt_name, gi, sched):
+    """The 512-thread fused kernel (twice the warps per staged query, lists of up to 4096
+    candidates selected on chip) returns exactly what the stand-alone scoring and top-kappa
+    return, for both lane counts it is built for, with and without the work plan."""
+    dt = glv.DTYPES[dt_name]
+    G = glv.SCORE_GROUPS[dt][gi]
+    try:
+        glv.glv_set_score_config(dt, G, 0, 0, sched)
+        assert glv.glv_get_score_config(dt, 40)[3] == sched
+        for kappa in (100, 200):
+            test_score_topk_fused_matches_separate(glv, dt_name, 700, kappa)
     finally:
         glv.glv_set_score_config(dt, 0, 0)
 
