@@ -17,10 +17,10 @@
 //               from TMEM (twice for FP8: the row maximum first), converts, and writes the row
 //               of the store (zero padding up to the 16-byte boundary);
 //   warps 5..12 loaders: gather the tile's 128 X rows (through the permutation) and B_c's rows
-//               with 16-byte loads, split them into hi / lo and write both into the 128-byte
-//               swizzled K-major layout the MMA descriptors read; the loads of the next K
-//               slice are in flight while one slice is split and stored (three stages of
-//               shared memory where they fit, else two).
+//               with 16-byte asynchronous copies (cp.async) straight into the 128-byte swizzled
+//               K-major layout the MMA descriptors read, then split each landed chunk in place
+//               into hi and lo; the copies of the next stages - 1 K slices are in flight while
+//               one slice is split (three stages of shared memory where they fit, else two).
 // Every mbarrier wait is bounded (tc.cuh): a timeout sets GLV_ERR_TIMEOUT, all roles leave,
 // the MMAs are drained and the TMEM is freed before the CTA exits.
 #include <cuda_bf16.h>
@@ -64,6 +64,21 @@ __host__ __device__ inline size_t bt_smem_bytes(int Npad, int C, int stages) {
 // Byte offset of 16-byte chunk c of row r in a 128-byte swizzled K-major tile (8-row atoms
 // of 1024 bytes; chunk positions XOR-ed with the row within the atom), as TMA would write it.
 GLV_DEV uint32_t sw128_off(int r, int c) { return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4)); }
+
+// 16-byte asynchronous copy global -> shared (cp.async.cg, L1 bypassed); src_bytes = 0 writes
+// zeros.  Copies are grouped per commit; wait_group_p(n) waits until at most n groups of this
+// thread are pending.
+GLV_DEV void bt_cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+GLV_DEV void bt_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+GLV_DEV void bt_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// n is 0 .. kBtMaxStages - 2 (wait_group takes an immediate)
+GLV_DEV void bt_cp_async_wait_group_p(int n) {
+  if (n <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  else asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
 
 GLV_DEV void split_tf32(float4 v, float4& h, float4& l) {
   h.x = __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
@@ -294,81 +309,107 @@ __global__ void __launch_bounds__(kBtThreads, 1) build_tc_kernel(const BuildTcAr
     }
   } else {
     // ---------------- loaders ----------------
+    // The K slices of this CTA's tiles form one sequence.  Each thread copies its 16-byte chunks
+    // of slice g + P (asynchronously, cp.async: no registers held) while it splits the chunks
+    // of slice g, which landed earlier: P = stages - 1 slices are in flight.  A slice's raw FP32
+    // chunks land where their hi parts go; the split rewrites them in place and writes lo.
     const int i = threadIdx.x - 5 * 32;  // 0 .. 255
     const int c16 = i & 7;              // the 16-byte chunk of K this thread handles
     const int nb = (a.Npad * 8 + 255) / 256;  // B chunk jobs per thread (<= 8)
-    int stage = 0;
-    uint32_t phase = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+    const int P = nst - 1;
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total = (int64_t)my_tiles * nkb;
+    // issue stream state
+    int it = 0, ikb = 0, istage = 0;
+    uint32_t iphase = 0;
+    const float* xr[4] = {nullptr, nullptr, nullptr, nullptr};
+    const float* Bc = a.B;
+    auto set_tile = [&](int t) {
       int c, row0, nrows;
       tile_of(t, c, row0, nrows);
-      const float* xr[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int r = (i >> 3) + 32 * u;
         xr[u] = r < nrows ? a.X + (int64_t)a.perm[row0 + r] * a.D : nullptr;
       }
-      const float* Bc = a.B + (int64_t)c * a.d * a.D;
-      // the 16-byte chunks of K slice kb this thread handles: 4 of X rows, nb of B_c rows
-      float4 va[4], vb[8];
-      auto load_slice = [&](int kb) {
-        const int k = kb * kBtK + c16 * 4;  // first K element of this thread's chunk
-        const bool kin = k < a.D;           // D % 4 == 0: a chunk is all in or all out
+      Bc = a.B + (int64_t)c * a.d * a.D;
+    };
+    bool ok = true;
+    // copies of the next slice of the issue stream into its stage (once the MMAs have freed it)
+    auto issue = [&]() -> bool {
+      int w_ok = 1;
+      if (lane == 0) w_ok = tc::mbar_wait(&empty[istage], iphase ^ 1, abort_flag) ? 1 : 0;
+      w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+      if (!w_ok) return false;
+      if (ikb == 0) set_tile(blockIdx.x + it * gridDim.x);
+      const int k = ikb * kBtK + c16 * 4;
+      const bool kin = k < a.D;  // D % 4 == 0: a chunk is all in or all out
+      uint8_t* base = smem + (size_t)istage * sb;
+      uint8_t* ahi = base;
+      uint8_t* bhi = base + 2 * kBtM * 128;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          va[u] = (xr[u] && kin) ? *reinterpret_cast<const float4*>(xr[u] + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < 4; ++u) {
+        const int r = (i >> 3) + 32 * u;
+        const bool in = xr[u] != nullptr && kin;
+        bt_cp_async16(ahi + sw128_off(r, c16), in ? xr[u] + k : a.X, in ? 16 : 0);
+      }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int r = (i >> 3) + 32 * j;
-          vb[j] = (j < nb && r < a.d && kin) ? __ldg(reinterpret_cast<const float4*>(Bc + (int64_t)r * a.D + k))
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      };
-      load_slice(0);
-      for (int kb = 0; kb < nkb; ++kb) {
-        int w_ok = 1;
-        if (lane == 0) w_ok = tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag) ? 1 : 0;
-        w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
-        if (!w_ok) {
-          ok = false;
-          break;
-        }
-        const float4 ca[4] = {va[0], va[1], va[2], va[3]};
-        const float4 cb[8] = {vb[0], vb[1], vb[2], vb[3], vb[4], vb[5], vb[6], vb[7]};
-        if (kb + 1 < nkb) load_slice(kb + 1);  // in flight while this slice is split and stored
-        uint8_t* base = smem + (size_t)stage * sb;
-        uint8_t* ahi = base;
-        uint8_t* alo = base + kBtM * 128;
-        uint8_t* bhi = base + 2 * kBtM * 128;
-        uint8_t* blo = bhi + (size_t)a.Npad * 128;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = (i >> 3) + 32 * u;
-          float4 h, l;
-          split_tf32(ca[u], h, l);
-          *reinterpret_cast<float4*>(ahi + sw128_off(r, c16)) = h;
-          *reinterpret_cast<float4*>(alo + sw128_off(r, c16)) = l;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int r = (i >> 3) + 32 * j;
-          if (j < nb && r < a.Npad) {
-            float4 h, l;
-            split_tf32(cb[j], h, l);
-            *reinterpret_cast<float4*>(bhi + sw128_off(r, c16)) = h;
-            *reinterpret_cast<float4*>(blo + sw128_off(r, c16)) = l;
-          }
-        }
-        tc::fence_proxy_async_smem();  // the MMA reads these through the async proxy
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&full[stage]);
-        if (++stage == nst) {
-          stage = 0;
-          phase ^= 1;
+      for (int j = 0; j < 8; ++j) {
+        const int r = (i >> 3) + 32 * j;
+        if (j < nb && r < a.Npad) {
+          const bool in = r < a.d && kin;
+          bt_cp_async16(bhi + sw128_off(r, c16), in ? Bc + (int64_t)r * a.D + k : a.B, in ? 16 : 0);
         }
       }
+      if (++ikb == nkb) {
+        ikb = 0;
+        ++it;
+      }
+      if (++istage == nst) {
+        istage = 0;
+        iphase ^= 1;
+      }
+      return true;
+    };
+    for (int q = 0; q < P; ++q) {  // P groups (empty ones past the end): P pending below
+      if (q < total && ok) ok = issue();
+      bt_cp_async_commit();
     }
+    int sstage = 0;
+    for (int64_t g = 0; ok && g < total; ++g) {
+      bt_cp_async_wait_group_p(P - 1);  // this thread's copies of slice g have landed
+      uint8_t* base = smem + (size_t)sstage * sb;
+      uint8_t* ahi = base;
+      uint8_t* alo = base + kBtM * 128;
+      uint8_t* bhi = base + 2 * kBtM * 128;
+      uint8_t* blo = bhi + (size_t)a.Npad * 128;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = (i >> 3) + 32 * u;
+        float4 h, l;
+        split_tf32(*reinterpret_cast<const float4*>(ahi + sw128_off(r, c16)), h, l);
+        *reinterpret_cast<float4*>(ahi + sw128_off(r, c16)) = h;
+        *reinterpret_cast<float4*>(alo + sw128_off(r, c16)) = l;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int r = (i >> 3) + 32 * j;
+        if (j < nb && r < a.Npad) {
+          float4 h, l;
+          split_tf32(*reinterpret_cast<const float4*>(bhi + sw128_off(r, c16)), h, l);
+          *reinterpret_cast<float4*>(bhi + sw128_off(r, c16)) = h;
+          *reinterpret_cast<float4*>(blo + sw128_off(r, c16)) = l;
+        }
+      }
+      tc::fence_proxy_async_smem();  // the MMA reads these through the async proxy
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&full[sstage]);
+      if (++sstage == nst) sstage = 0;
+      // then the copies of slice g + P, into the stage slice g - 1 leaves (the MMA has it)
+      if (g + P < total) ok = issue();
+      bt_cp_async_commit();  // (empty when nothing was issued: one group per slice)
+    }
+    bt_cp_async_wait_all();  // no copy may land in shared memory after the CTA has left
   }
 
   tc::tc_fence_before();

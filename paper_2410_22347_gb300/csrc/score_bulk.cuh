@@ -114,16 +114,17 @@ GLV_DEV bool score_range_bulk(const ScoreArgs& a, const float* qs, uint8_t* ring
         const bool ok = okr && inr && tag < a.C;
         const float* qrow = qs + (ok ? tag : 0) * a.qstride;
         const uint8_t* row = slot + (size_t)rs * rb;
-        float acc = 0.f;
+        float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
           const int ch = gl + t * G;
           if (ch < a.nch) {
             uint4 x = ok ? lds128(row + ch * 16) : make_uint4(0, 0, 0, 0);
             if (ch == a.nch - 1 && a.tail < 16) x = keep_bytes(x, a.tail);
-            acc += dot_chunk<DT>(x, qrow, ch, a.sbs, g & 1);
+            dot_chunk<DT>(acc2, x, qrow, ch, a.sbs, g & 1);
           }
         }
+        float acc = acc2.x + acc2.y;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (inr && gl == 0) {
@@ -132,7 +133,7 @@ GLV_DEV bool score_range_bulk(const ScoreArgs& a, const float* qs, uint8_t* ring
             sv = -INFINITY;
             report(a.d_status, GLV_ERR_BAD_ID);
           } else if constexpr (DT == GLV_FP8_E4M3) {
-            sv = (acc * qp_scales(a, qs)[tag]) * sc;
+            sv = acc * sc;
           } else {
             sv = acc;
           }

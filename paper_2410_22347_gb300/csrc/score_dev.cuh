@@ -1,16 +1,15 @@
 // score_dev.cuh -- device-side body of the gather-score (Algorithm 4, procedure
 // inner-product; Eq. GleanVec approximation, Section 4), shared by the stand-alone scoring
-// kernel and the fused score + top-kappa kernel so both compute bit-identical scores.
+// kernel, the fused score + top-kappa kernel and the lazy kernel, so all compute bit-identical
+// scores.
 //
-// A group of G lanes scores one candidate: the lanes issue all of their 16-byte loads of
-// the reduced row (NCH each) before any arithmetic, so a warp keeps 32 x NCH x 16 bytes in
-// flight; partial dots are combined with xor-shuffles inside the group.  Rows are decoded in
-// registers: FP32 as is, BF16 by shifting into the high half of an FP32 word.  FP8-e4m3 codes
-// are converted two at a time to f16 (exact: every e4m3 value is an f16 value) and multiplied
-// with mixed-precision FMAs (f16 x f16 products, FP32 accumulation) against the projected
-// query held as two f16 terms per element, q * 2^sigma_c = hi + lo (22 significant bits; the
-// power of two 2^sigma_c per cluster keeps both terms in f16's normal range).  The cluster's
-// 2^-sigma_c and the row scale are applied once to the finished dot.
+// A group of G lanes scores one candidate: the lanes issue all of their 16-byte loads of the
+// reduced row (NCH each) before any arithmetic, so a warp keeps 32 x NCH x 16 bytes in flight;
+// partial dots are combined with xor-shuffles inside the group.  Rows are decoded in
+// registers -- FP32 as is, BF16 by shifting into the high half of an FP32 word, FP8-e4m3 two
+// codes at a time into f16 (exact: every e4m3 value is an f16 value) and then FP32 -- and
+// multiplied with the FP32 projected query by packed two-way FMAs (FP32 accumulation).  The
+// row scale of an FP8 row is applied once to the finished dot.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -38,87 +37,74 @@ struct Elem<GLV_FP8_E4M3> {
   static constexpr int kBytes = 1;
 };
 
-// Four FP8-e4m3 codes (the bytes of x, element 0 in the low byte) against the projected-query
-// terms of the same four elements, q = [hi(0,1), hi(2,3), lo(0,1), lo(2,3)] as f16 pairs:
-// sh += sum_e x_e * hi_e, sl += sum_e x_e * lo_e, element by element in order (each product
-// exact, each sum rounded to FP32).
-GLV_DEV void fp8_word_dot(uint32_t x, float4 q, float& sh, float& sl) {
+// Four FP8-e4m3 codes (the bytes of x, element 0 in the low byte) against four FP32 query
+// elements q: each pair of codes becomes an f16 pair (hardware conversion, exact), each f16 an
+// FP32 value (exact), and two packed FMAs accumulate elements 0, 1 into (acc.x, acc.y) and
+// then elements 2, 3 into the same pair.
+GLV_DEV void fp8_word_dot(uint32_t x, float4 q, float2& acc) {
+  float f0, f1, f2, f3;
   asm("{\n\t"
-      ".reg .b16 c01, c23, x0, x1, x2, x3, h0, h1, h2, h3, l0, l1, l2, l3;\n\t"
+      ".reg .b16 c01, c23, h0, h1, h2, h3;\n\t"
       ".reg .b32 p01, p23;\n\t"
-      "mov.b32 {c01, c23}, %2;\n\t"
+      "mov.b32 {c01, c23}, %4;\n\t"
       "cvt.rn.f16x2.e4m3x2 p01, c01;\n\t"
       "cvt.rn.f16x2.e4m3x2 p23, c23;\n\t"
-      "mov.b32 {x0, x1}, p01;\n\t"
-      "mov.b32 {x2, x3}, p23;\n\t"
-      "mov.b32 {h0, h1}, %3;\n\t"
-      "mov.b32 {h2, h3}, %4;\n\t"
-      "mov.b32 {l0, l1}, %5;\n\t"
-      "mov.b32 {l2, l3}, %6;\n\t"
-      "fma.rn.f32.f16 %0, x0, h0, %0;\n\t"
-      "fma.rn.f32.f16 %1, x0, l0, %1;\n\t"
-      "fma.rn.f32.f16 %0, x1, h1, %0;\n\t"
-      "fma.rn.f32.f16 %1, x1, l1, %1;\n\t"
-      "fma.rn.f32.f16 %0, x2, h2, %0;\n\t"
-      "fma.rn.f32.f16 %1, x2, l2, %1;\n\t"
-      "fma.rn.f32.f16 %0, x3, h3, %0;\n\t"
-      "fma.rn.f32.f16 %1, x3, l3, %1;\n\t"
+      "mov.b32 {h0, h1}, p01;\n\t"
+      "mov.b32 {h2, h3}, p23;\n\t"
+      "cvt.f32.f16 %0, h0;\n\t"
+      "cvt.f32.f16 %1, h1;\n\t"
+      "cvt.f32.f16 %2, h2;\n\t"
+      "cvt.f32.f16 %3, h3;\n\t"
       "}"
-      : "+f"(sh), "+f"(sl)
-      : "r"(x), "r"(__float_as_uint(q.x)), "r"(__float_as_uint(q.y)), "r"(__float_as_uint(q.z)),
-        "r"(__float_as_uint(q.w)));
+      : "=f"(f0), "=f"(f1), "=f"(f2), "=f"(f3)
+      : "r"(x));
+  acc = __ffma2_rn(make_float2(q.x, q.y), make_float2(f0, f1), acc);
+  acc = __ffma2_rn(make_float2(q.z, q.w), make_float2(f2, f3), acc);
 }
 
 // Dot product of one 16-byte chunk of a reduced row with the matching projected-query
-// elements.  The projected query of a cluster is laid out in shared memory as EPC/4
+// elements, accumulated into a pair of FP32 partial sums (acc.x + acc.y is the dot once every
+// chunk has been added; even elements go to acc.x, odd ones to acc.y).
+// The projected query of a cluster is laid out in shared memory as EPC/4
 // sub-blocks of float4 (stride sbs), each sub-block holding the same 4-element slice of every
 // chunk: element (chunk ch, e) sits at float4 index (e / 4) * sbs + ch.  Lanes that read
 // consecutive chunks of one row read consecutive float4 words.  When a quarter-warp serves two
 // candidates, the odd one (sw = 1) walks the sub-blocks in swapped order (BF16: 1,0; FP8:
 // 2,3,0,1), which with the padded sub-block stride puts the two candidates' reads 64 bytes
-// apart modulo 128 -- in opposite halves of the banks.  The FP32 sum follows the walk order,
+// apart modulo 128 -- in opposite halves of the banks.  The FP32 sums follow the walk order,
 // so a candidate's result depends on the parity of its position in its group, which every
 // kernel derives from its offset in the candidate list.
 template <int DT>
-GLV_DEV float dot_chunk(uint4 v, const float* qrow, int ch, int sbs, int sw) {
+GLV_DEV void dot_chunk(float2& acc, uint4 v, const float* qrow, int ch, int sbs, int sw) {
   const float4* q4 = reinterpret_cast<const float4*>(qrow);
   if constexpr (DT == GLV_F32) {
-    float4 a = q4[ch];
-    return a.x * __uint_as_float(v.x) + a.y * __uint_as_float(v.y) + a.z * __uint_as_float(v.z) +
-           a.w * __uint_as_float(v.w);
+    const float4 a = q4[ch];
+    acc = __ffma2_rn(make_float2(a.x, a.y), make_float2(__uint_as_float(v.x), __uint_as_float(v.y)), acc);
+    acc = __ffma2_rn(make_float2(a.z, a.w), make_float2(__uint_as_float(v.z), __uint_as_float(v.w)), acc);
   } else {
     // odd lane groups walk the two halves of the chunk in swapped order; the words are picked
     // with selects (a runtime index into a register array would put it in local memory)
     const uint32_t x0 = sw ? v.z : v.x, x1 = sw ? v.w : v.y;
     const uint32_t x2 = sw ? v.x : v.z, x3 = sw ? v.y : v.w;
-    const float4* qa = q4 + sw * sbs + ch;
-    const float4* qb = q4 + (sw ^ 1) * sbs + ch;
-    float s = 0.f;
     if constexpr (DT == GLV_BF16) {
-      // sub-block 0 holds elements 0..3 (words 0, 1), sub-block 1 elements 4..7 (words 2, 3)
-      const float4 a = *qa, b = *qb;
-      s = fmaf(a.x, __uint_as_float(x0 << 16), s);
-      s = fmaf(a.y, __uint_as_float(x0 & 0xffff0000u), s);
-      s = fmaf(a.z, __uint_as_float(x1 << 16), s);
-      s = fmaf(a.w, __uint_as_float(x1 & 0xffff0000u), s);
-      s = fmaf(b.x, __uint_as_float(x2 << 16), s);
-      s = fmaf(b.y, __uint_as_float(x2 & 0xffff0000u), s);
-      s = fmaf(b.z, __uint_as_float(x3 << 16), s);
-      s = fmaf(b.w, __uint_as_float(x3 & 0xffff0000u), s);
+      // sub-block 0 holds elements 0..3 (words 0, 1), sub-block 1 elements 4..7 (words 2, 3);
+      // the low half of a word is the even element
+      const float4 a = q4[sw * sbs + ch], b = q4[(sw ^ 1) * sbs + ch];
+      acc = __ffma2_rn(make_float2(a.x, a.y), make_float2(__uint_as_float(x0 << 16), __uint_as_float(x0 & 0xffff0000u)),
+                       acc);
+      acc = __ffma2_rn(make_float2(a.z, a.w), make_float2(__uint_as_float(x1 << 16), __uint_as_float(x1 & 0xffff0000u)),
+                       acc);
+      acc = __ffma2_rn(make_float2(b.x, b.y), make_float2(__uint_as_float(x2 << 16), __uint_as_float(x2 & 0xffff0000u)),
+                       acc);
+      acc = __ffma2_rn(make_float2(b.z, b.w), make_float2(__uint_as_float(x3 << 16), __uint_as_float(x3 & 0xffff0000u)),
+                       acc);
     } else {
-      // sub-block t holds the terms of the four elements of word t as f16 pairs
-      // [hi(0,1), hi(2,3), lo(0,1), lo(2,3)]; odd groups take the words in the order 2, 3, 0, 1.
-      // The hi and lo products accumulate in two chains, added at the end.
+      // sub-block t holds the four elements of word t; odd groups take the words in the order
+      // 2, 3, 0, 1
       const uint32_t xs[4] = {x0, x1, x2, x3};
-      float sl = 0.f;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const float4 a = q4[(t ^ (sw << 1)) * sbs + ch];
-        fp8_word_dot(xs[t], a, s, sl);
-      }
-      s += sl;
+      for (int t = 0; t < 4; ++t) fp8_word_dot(xs[t], q4[(t ^ (sw << 1)) * sbs + ch], acc);
     }
-    return s;
   }
 }
 
@@ -181,69 +167,11 @@ GLV_DEV float warp_max(float v) {
   return v;
 }
 
-// FP8 rows: the per-cluster factors 2^-sigma_c follow the C rows of projected views.
-GLV_DEV float* qp_scales(const ScoreArgs& a, float* qs) { return qs + (size_t)a.C * a.qstride; }
-GLV_DEV const float* qp_scales(const ScoreArgs& a, const float* qs) { return qs + (size_t)a.C * a.qstride; }
-
-// FP8 rows: turn the FP32 projected views staged in the sub-block layout into the f16 term
-// pairs dot_chunk reads, in place, one warp per cluster row (rows with seen[c] == 0 skipped
-// when seen is given).  sigma_c = 14 - floor(log2 max_e |q_c,e|) (clamped to +-126) puts the
-// largest |q| * 2^sigma_c in [2^14, 2^15); hi = f16(q 2^sigma_c), lo = f16(q 2^sigma_c - hi)
-// (the difference is exact in FP32), so hi + lo holds q 2^sigma_c to 22 significant bits.
-// Each 16-byte slot holding elements 4t..4t+3 of a chunk becomes
-// [hi(0,1), hi(2,3), lo(0,1), lo(2,3)], and 2^-sigma_c goes to qp_scales.
-GLV_DEV void split_qp_fp8(const ScoreArgs& a, float* qs, const uint8_t* seen) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int slots = a.nch * 4;  // 16-byte slots per row: 4 sub-blocks of nch chunks
-  float* qsc = qp_scales(a, qs);
-  for (int c = warp; c < a.C; c += nwarps) {
-    if (seen && !seen[c]) continue;
-    float4* row = reinterpret_cast<float4*>(qs + (size_t)c * a.qstride);
-    float m = 0.f;
-    for (int t = lane; t < slots; t += 32) {
-      const int u = t / a.nch, ch = t - u * a.nch;
-      const float4 v = row[u * a.sbs + ch];
-      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-    }
-    m = warp_max(m);
-    int sigma = 0;
-    if (m > 0.f && m <= 3.4e38f) {
-      const int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m); -127 if subnormal
-      sigma = min(126, max(-126, 14 - e));
-    }
-    const float up = __uint_as_float((uint32_t)(127 + sigma) << 23);
-    const float down = __uint_as_float((uint32_t)(127 - sigma) << 23);
-    for (int t = lane; t < slots; t += 32) {
-      const int u = t / a.nch, ch = t - u * a.nch;
-      const float4 v = row[u * a.sbs + ch];
-      const float f[4] = {v.x * up, v.y * up, v.z * up, v.w * up};
-      __half h[4], l[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        h[k] = __float2half_rn(f[k]);
-        l[k] = __float2half_rn(f[k] - __half2float(h[k]));
-      }
-      float4 o;
-      o.x = __uint_as_float((uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16));
-      o.y = __uint_as_float((uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16));
-      o.z = __uint_as_float((uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16));
-      o.w = __uint_as_float((uint32_t)__half_as_ushort(l[2]) | ((uint32_t)__half_as_ushort(l[3]) << 16));
-      row[u * a.sbs + ch] = o;
-    }
-    if (lane == 0) qsc[c] = down;
-  }
-}
-
 // Stage the C projected views of query j into shared memory in the sub-block layout of
-// dot_chunk (rows of a.qstride floats; elements d..dpad-1 are zero); FP8 rows then get their
-// f16 term pairs (split_qp_fp8).  Called by the whole CTA.
+// dot_chunk (rows of a.qstride floats; elements d..dpad-1 are zero).  Called by the whole CTA.
 template <int DT>
 GLV_DEV void stage_qp(const ScoreArgs& a, int64_t j, float* qs) {
   stage_qp_f32<DT>(a, j, qs);
-  if constexpr (DT == GLV_FP8_E4M3) {
-    __syncthreads();
-    split_qp_fp8(a, qs, nullptr);
-  }
 }
 
 // 16-byte asynchronous copy global -> shared that bypasses L1 (cp.async.cg); src_bytes < 16
@@ -253,11 +181,10 @@ GLV_DEV void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
 }
 
-// Whether stage_qp_async can stage this problem's projected views (the float4 layout; FP8
-// rows need the f16 terms computed, so they are staged by stage_qp).
+// Whether stage_qp_async can stage this problem's projected views (the float4 layout).
 template <int DT>
 GLV_DEV bool qp_async_ok(const ScoreArgs& a) {
-  return DT != GLV_FP8_E4M3 && (a.d & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Qp) & 15) == 0;
+  return (a.d & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Qp) & 15) == 0;
 }
 
 // stage_qp's float4 path as asynchronous copies: every float4 of the query's C projected views
@@ -312,16 +239,17 @@ GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, 
                         Sink& sink) {
   const bool ok = r.ok && r.tag < a.C;
   const float* qrow = qs + (ok ? r.tag : 0) * a.qstride;
-  float acc = 0.f;
+  float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
   for (int t = 0; t < NCH; ++t) {
     const int ch = gl + t * G;
     if (ch < a.nch) {
       uint4 x = r.v[t];
       if (ch == a.nch - 1 && a.tail < 16) x = keep_bytes(x, a.tail);
-      acc += dot_chunk<DT>(x, qrow, ch, a.sbs, sw);
+      dot_chunk<DT>(acc2, x, qrow, ch, a.sbs, sw);
     }
   }
+  float acc = acc2.x + acc2.y;
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (r.in && gl == 0) {
@@ -330,7 +258,7 @@ GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, 
       s = -INFINITY;
       report(a.d_status, GLV_ERR_BAD_ID);
     } else if constexpr (DT == GLV_FP8_E4M3) {
-      s = (acc * qp_scales(a, qs)[r.tag]) * r.sc;
+      s = acc * r.sc;
     } else {
       s = acc;
     }

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(256) score_lazy_kernel(const ScoreArgs a, cons
                                                          const float* __restrict__ A, int32_t* __restrict__ visited) {
   extern __shared__ __align__(16) float smem[];
   float* qs = smem;                                          // C x qstride projected views
-  float* qv = qs + (size_t)a.C * (a.qstride + 1);            // (C factors for FP8 rows,) the query
+  float* qv = qs + (size_t)a.C * a.qstride;                  // the query
   uint8_t* seen = reinterpret_cast<uint8_t*>(qv + D);        // C flags
   constexpr int EPC = Elem<DT>::kPerChunk;
   const int64_t j = blockIdx.x;
@@ -55,10 +55,6 @@ __global__ void __launch_bounds__(256) score_lazy_kernel(const ScoreArgs a, cons
   }
   if (threadIdx.x == 0 && visited) visited[j] = nvis;
   __syncthreads();
-  if constexpr (DT == GLV_FP8_E4M3) {  // the same f16 terms the eager kernels stage
-    split_qp_fp8(a, qs, seen);
-    __syncthreads();
-  }
   float* scores = a.scores;
   score_range<DT, G, NCH, false>(a, qs, p0, p1, [scores](int64_t p, float s) { scores[p] = s; });
 }
@@ -89,7 +85,7 @@ struct LazyLaunch {
 size_t lazy_smem_bytes(int C, int d, int D, int dt) {
   const int eb = dt == GLV_F32 ? 4 : (dt == GLV_BF16 ? 2 : 1);
   const int qstride = qp_qstride((d * eb + 15) / 16, dt);
-  return (size_t)C * (qstride + 1) * 4 + (size_t)D * 4 + (size_t)C + 16;
+  return (size_t)C * qstride * 4 + (size_t)D * 4 + (size_t)C + 16;
 }
 
 cudaError_t launch_score_lazy(const ScoreArgs& a0, int dt, int64_t nq, const float* Q, int D, const float* A,

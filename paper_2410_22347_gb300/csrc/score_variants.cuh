@@ -31,8 +31,8 @@ struct ScoreSmem {
 __host__ __device__ inline ScoreSmem score_smem(int C, int qstride, bool fused, int mode, int RB, int nch,
                                                 int kappa = 0, int cache = kFusedCache) {
   ScoreSmem m;
-  // the C rows of projected views, then C per-cluster factors (used by FP8 rows)
-  m.qs_bytes = (((size_t)C * (qstride + 1) * sizeof(float)) + 127) & ~size_t(127);
+  // the C rows of projected views
+  m.qs_bytes = (((size_t)C * qstride * sizeof(float)) + 127) & ~size_t(127);
   m.keys_bytes = fused ? (((size_t)cache * sizeof(uint32_t) + (size_t)kappa * 8) + 127) & ~size_t(127) : 0;
   const int warps = kScoreThreads / 32;
   m.ring_bytes = mode == 2 ? (size_t)warps * kBulkSlots * RB * nch * 16 : 0;
