@@ -25,21 +25,23 @@ struct ScoreArgs {
 };
 
 // Shared-memory layout of a projected-query row (see dot_chunk in score_dev.cuh): EPC/4
-// sub-blocks of sbs float4 each.  For BF16 and FP8 rows the sub-block stride is padded so that
-// the two candidates a quarter-warp serves read opposite halves of the banks (odd candidate
-// groups walk the sub-blocks in swapped order); rows then start on 128-byte boundaries.
+// sub-blocks of sbs float4 each.  BF16 rows: the sub-block stride is padded so that the two
+// candidates a quarter-warp serves read opposite halves of the banks (odd candidate groups walk
+// the two sub-blocks in swapped order); rows then start on 128-byte boundaries.  FP8 rows:
+// sub-blocks are not padded, and the row stride is an odd multiple of 64 bytes, so rows of
+// consecutive clusters start in opposite halves of the banks.  FP32 rows: one sub-block, rows
+// padded by 16 bytes.
 __host__ __device__ inline int qp_sub_blocks(int dt) { return dt == 0 ? 1 : (dt == 1 ? 2 : 4); }
 __host__ __device__ inline int qp_sbs(int nch, int dt) {
-  if (dt == 0) return nch;
+  if (dt != 1) return nch;
   int s = nch;
-  if (dt == 1)
-    while (s % 8 != 4) ++s;  // 16 * s = 64 (mod 128)
-  else
-    while (s % 4 != 2) ++s;  // 32 * s = 64 (mod 128)
+  while (s % 8 != 4) ++s;  // 16 * s = 64 (mod 128)
   return s;
 }
 __host__ __device__ inline int qp_qstride(int nch, int dt) {
-  return dt == 0 ? nch * 4 + 4 : qp_sub_blocks(dt) * qp_sbs(nch, dt) * 4;
+  if (dt == 0) return nch * 4 + 4;
+  if (dt == 1) return 2 * qp_sbs(nch, dt) * 4;
+  return 16 * nch + ((nch & 1) ? 0 : 16);  // 64 * nch bytes, plus 64 when that is a multiple of 128
 }
 
 struct RerankArgs {

@@ -121,7 +121,7 @@ GLV_DEV bool score_range_bulk(const ScoreArgs& a, const float* qs, uint8_t* ring
           if (ch < a.nch) {
             uint4 x = ok ? lds128(row + ch * 16) : make_uint4(0, 0, 0, 0);
             if (ch == a.nch - 1 && a.tail < 16) x = keep_bytes(x, a.tail);
-            dot_chunk<DT>(acc2, x, qrow, ch, a.sbs, g & 1);
+            dot_chunk<DT>(acc2, x, qrow, ch, a.sbs, odd_group_swaps<DT>() ? (g & 1) : 0);
           }
         }
         float acc = acc2.x + acc2.y;

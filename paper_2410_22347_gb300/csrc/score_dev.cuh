@@ -62,18 +62,30 @@ GLV_DEV void fp8_word_dot(uint32_t x, float4 q, float2& acc) {
   acc = __ffma2_rn(make_float2(q.z, q.w), make_float2(f2, f3), acc);
 }
 
+// Whether the odd lane groups of a quarter-warp walk the sub-blocks of a chunk in swapped
+// order (dot_chunk).  BF16 rows do: that keeps the two candidates' shared-memory reads in
+// opposite halves of the banks.  For FP8 rows the four selects per chunk cost more than the
+// conflicts they avoid (measured), so FP8 rows keep the natural order and their view rows are
+// laid out so that rows of consecutive clusters start in opposite bank halves
+// (qp_qstride): two candidates then conflict only when their clusters' rows share a half.
+template <int DT>
+constexpr bool odd_group_swaps() {
+  return DT == GLV_BF16;
+}
+
 // Dot product of one 16-byte chunk of a reduced row with the matching projected-query
 // elements, accumulated into a pair of FP32 partial sums (acc.x + acc.y is the dot once every
 // chunk has been added; even elements go to acc.x, odd ones to acc.y).
 // The projected query of a cluster is laid out in shared memory as EPC/4
 // sub-blocks of float4 (stride sbs), each sub-block holding the same 4-element slice of every
 // chunk: element (chunk ch, e) sits at float4 index (e / 4) * sbs + ch.  Lanes that read
-// consecutive chunks of one row read consecutive float4 words.  When a quarter-warp serves two
-// candidates, the odd one (sw = 1) walks the sub-blocks in swapped order (BF16: 1,0; FP8:
-// 2,3,0,1), which with the padded sub-block stride puts the two candidates' reads 64 bytes
-// apart modulo 128 -- in opposite halves of the banks.  The FP32 sums follow the walk order,
-// so a candidate's result depends on the parity of its position in its group, which every
-// kernel derives from its offset in the candidate list.
+// consecutive chunks of one row read consecutive float4 words.  For BF16 rows, when a
+// quarter-warp serves two candidates, the odd one (sw = 1) walks the two sub-blocks in
+// swapped order, which with the padded sub-block stride puts the two candidates' reads 64
+// bytes apart modulo 128 -- in opposite halves of the banks.  The FP32 sums follow the walk
+// order, so a BF16 candidate's result depends on the parity of its position in its group,
+// which every kernel derives from its offset in the candidate list.  (sw is 0 for the other
+// store types: see odd_group_swaps.)
 template <int DT>
 GLV_DEV void dot_chunk(float2& acc, uint4 v, const float* qrow, int ch, int sbs, int sw) {
   const float4* q4 = reinterpret_cast<const float4*>(qrow);
@@ -99,8 +111,8 @@ GLV_DEV void dot_chunk(float2& acc, uint4 v, const float* qrow, int ch, int sbs,
       acc = __ffma2_rn(make_float2(b.z, b.w), make_float2(__uint_as_float(x3 << 16), __uint_as_float(x3 & 0xffff0000u)),
                        acc);
     } else {
-      // sub-block t holds the four elements of word t; odd groups take the words in the order
-      // 2, 3, 0, 1
+      // sub-block t holds the four elements of word t (with sw = 1 the words would be taken in
+      // the order 2, 3, 0, 1)
       const uint32_t xs[4] = {x0, x1, x2, x3};
 #pragma unroll
       for (int t = 0; t < 4; ++t) fp8_word_dot(xs[t], q4[(t ^ (sw << 1)) * sbs + ch], acc);
@@ -234,7 +246,7 @@ GLV_DEV void load_row(const ScoreArgs& a, RowLoad<DT, G, NCH, PIPE>& r, int64_t 
   if constexpr (DT == GLV_FP8_E4M3) r.sc = r.ok ? __ldg(a.scales + id) : 0.f;
 }
 
-template <int DT, int G, int NCH, bool PIPE, class Sink>
+template <int DT, int G, int NCH, bool PIPE, bool TAIL, class Sink>
 GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, const float* qs, int gl, int sw,
                         Sink& sink) {
   const bool ok = r.ok && r.tag < a.C;
@@ -245,7 +257,9 @@ GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, 
     const int ch = gl + t * G;
     if (ch < a.nch) {
       uint4 x = r.v[t];
-      if (ch == a.nch - 1 && a.tail < 16) x = keep_bytes(x, a.tail);
+      if constexpr (TAIL) {
+        if (ch == a.nch - 1) x = keep_bytes(x, a.tail);
+      }
       dot_chunk<DT>(acc2, x, qrow, ch, a.sbs, sw);
     }
   }
@@ -266,13 +280,14 @@ GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, 
   }
 }
 
-template <int DT, int G, int NCH, bool PIPE, class Sink>
-GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_t b1, Sink sink) {
+template <int DT, int G, int NCH, bool PIPE, bool TAIL, class Sink>
+GLV_DEV void score_range_t(const ScoreArgs& a, const float* qs, int64_t b0, int64_t b1, Sink& sink) {
   constexpr int GPW = kWarp / G;
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int g = lane / G, gl = lane % G;
+  const int sw = odd_group_swaps<DT>() ? (g & 1) : 0;
   const int64_t step = (int64_t)nwarps * GPW;
   int64_t base = b0 + (int64_t)warp * GPW;
   // the id of the next candidate is loaded one iteration ahead, so the row loads of an
@@ -285,7 +300,7 @@ GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_
       id_next = (p + step < b1) ? (int64_t)__ldg(a.ids + p + step) : 0;
       RowLoad<DT, G, NCH, PIPE> r;
       load_row(a, r, p, b1, id, gl);
-      finish_row(a, r, qs, gl, g & 1, sink);
+      finish_row<DT, G, NCH, PIPE, TAIL>(a, r, qs, gl, sw, sink);
     }
   } else {
     if (base >= b1) return;
@@ -303,10 +318,19 @@ GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_
         id_next = (pn + step < b1) ? (int64_t)__ldg(a.ids + pn + step) : 0;
         load_row(a, nxt, pn, b1, id, gl);
       }
-      finish_row(a, cur, qs, gl, g & 1, sink);
+      finish_row<DT, G, NCH, PIPE, TAIL>(a, cur, qs, gl, sw, sink);
       cur = nxt;
     }
   }
+}
+
+// Rows whose data end inside a 16-byte chunk (d * element bytes not a multiple of 16) need the
+// bytes past the data masked in that chunk; the loop is compiled twice and the kernel-uniform
+// choice is made once, so rows that end on a chunk boundary pay nothing for it.
+template <int DT, int G, int NCH, bool PIPE, class Sink>
+GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_t b1, Sink sink) {
+  if (a.tail < 16) score_range_t<DT, G, NCH, PIPE, true>(a, qs, b0, b1, sink);
+  else score_range_t<DT, G, NCH, PIPE, false>(a, qs, b0, b1, sink);
 }
 
 // Default lanes per candidate per store type: 8 for FP32 and BF16 rows, 4 for FP8 rows (the
