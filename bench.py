@@ -213,7 +213,7 @@ def source_sha(*rel):
 
 KERNEL_SOURCES = tuple("paper_2410_22347_gb300/csrc/" + f for f in (
     "score_variants.cuh", "score_dev.cuh", "score_launch.cuh", "score_bulk.cuh", "topk_dev.cuh", "common.cuh",
-    "kernels.cuh", "score.cu") + tuple(f"score_{t}_fused_m{m}.cu" for t in ("f32", "bf16", "fp8") for m in (0, 1)))
+    "kernels.cuh", "score.cu") + tuple(f"score_{t}_fused_{m}.cu" for t in ("f32", "bf16", "fp8") for m in ("m0", "m1", "w")))
 
 
 # DRAM bytes per candidate of the fused score + top-kappa kernel (dram__bytes_read.sum +
