@@ -234,10 +234,14 @@ __global__ void __launch_bounds__(TPB, fused_min_blocks_t(DT, MODE, NCH, TPB))
     const bool in_kc = lc <= kCache;
     const float* sj = scores + c0;
     const int32_t* ij = a.ids + c0;
+    // FP8 rows leave the kernel issue-bound: the survivors of long on-chip lists are ordered by
+    // the bitonic network there (fewer instructions); the other stores keep rank counting
+    constexpr bool kNetworkSort = DT == GLV_FP8_E4M3;
     if (nchunks == 1) {
       select_topk(
           S, lc, kappa, in_kc, [&](int64_t p) -> uint32_t { return in_kc ? kc[p] : score_key(sj[p]); },
-          [&](int64_t p) -> int32_t { return ij[p]; }, out_s + jj * kappa, out_id + jj * kappa);
+          [&](int64_t p) -> int32_t { return ij[p]; }, out_s + jj * kappa, out_id + jj * kappa, true,
+          kNetworkSort);
     } else {
       // the chunk's unordered top-kappa goes to the start of its own part of the scratch
       // (scores, then ids): every chunk has at least kChunk >= 2 kappa candidates, and its
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(TPB, fused_min_blocks_t(DT, MODE, NCH, TPB))
         select_topk(
             S, M, kappa, mc, [&](int64_t e) -> uint32_t { return mc ? kc[e] : score_key(__ldcg(ent(e))); },
             [&](int64_t e) -> int32_t { return __ldcg(reinterpret_cast<const int32_t*>(ent(e) + kap)); },
-            out_s + jj * kappa, out_id + jj * kappa);
+            out_s + jj * kappa, out_id + jj * kappa, true, kNetworkSort);
       }
     }
     __syncthreads();

@@ -331,6 +331,44 @@ GLV_DEV void rank_place_packed(const uint64_t* xs, int n, int kappa, float* out_
   }
 }
 
+// The same with a bitonic network (n <= blockDim.x, blockDim.x a power of two): one packed
+// value per thread over the first P = 2^ceil(log2 n) threads, partners closer than 32
+// exchanged by warp shuffles and farther ones through xs (whose values are all in registers
+// before the first exchange); the first kappa of the descending order are written.  Rank
+// counting costs about n^2 / 2 compares, the network P log2(P)^2 / 4 but with a barrier pair
+// per stage of stride >= 32: fewer instructions, more latency.
+// Threads past n hold 0, which sorts last (and equals the packing of a NaN score with id
+// INT32_MAX, so either order gives the same output).  All threads of the CTA must call it.
+GLV_DEV void bitonic_place_packed(uint64_t* xs, int n, int kappa, float* out_s, int32_t* out_id) {
+  const int t = threadIdx.x;
+  int P = 2;
+  while (P < n) P <<= 1;
+  uint64_t v = t < n ? xs[t] : 0ull;
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      uint64_t o = 0;
+      if (stride >= 32) {  // block-uniform branch: every thread reaches the barriers
+        if (t < P) xs[t] = v;
+        __syncthreads();
+        if (t < P) o = xs[t ^ stride];
+        __syncthreads();
+      } else if (t < ((P + 31) & ~31)) {
+        o = __shfl_xor_sync(0xffffffffu, v, stride);
+      }
+      if (t < P) {
+        const bool take_max = ((t & stride) == 0) == ((t & size) == 0);
+        const uint64_t mx = v > o ? v : o, mn = v > o ? o : v;
+        v = take_max ? mx : mn;
+      }
+    }
+  }
+  if (t < kappa) {
+    out_s[t] = key_score((uint32_t)(v >> 32));
+    out_id[t] = id_from_rank((uint32_t)v);
+  }
+}
+
 // Descending bitonic network over 32 E packed values held E per lane (element i = lane * E +
 // j) in one warp; sizes and strides are template parameters, so every register index is a
 // compile-time constant.
@@ -405,10 +443,12 @@ GLV_DEV void block_sort_write(TopkSmem& S, int n, uint64_t* xs, float* out_s, in
 // of candidate p in [0, L); `in_region` says whether the keys are the ones cached in S.region
 // (else S.region is free).  Writes kappa (score, id) pairs to out_s / out_id, sorted and
 // padded with (-inf, -1); with sorted == false, writes the min(L, kappa) selected pairs in no
-// particular order (a partial list for a later merge).  All threads of the CTA must call it.
+// particular order (a partial list for a later merge).  network_sort: order more than 256
+// threshold survivors with the bitonic network instead of rank counting (the choice of
+// instruction-bound callers).  All threads of the CTA must call it.
 template <class KeyOf, class IdOf>
 GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, bool in_region, KeyOf key_of, IdOf id_of,
-                         float* out_s, int32_t* out_id, bool sorted = true) {
+                         float* out_s, int32_t* out_id, bool sorted = true, bool network_sort = false) {
   if (threadIdx.x == 0) {
     S.count = 0;
     S.n_eq = 0;
@@ -427,10 +467,11 @@ GLV_DEV void select_topk(TopkSmem& S, int64_t L, int kappa, bool in_region, KeyO
     if (in_region && L <= (int64_t)kWarpThrKeys * blockDim.x && kappa <= kFilterMaxKappa &&
         S.region_words >= 2 * (int)blockDim.x) {
       const int n = warp_threshold_filter(S, (int)L, kappa, key_of, id_of);
-      const uint64_t* xs = reinterpret_cast<const uint64_t*>(S.region);
+      uint64_t* xs = reinterpret_cast<uint64_t*>(S.region);
       if (n >= 0) {
-        // kappa <= n <= blockDim.x: every rank below kappa is written
-        rank_place_packed(xs, n, kappa, out_s, out_id);
+        // kappa <= n <= blockDim.x: every rank below kappa is written (n is block-uniform)
+        if (network_sort && n > 256) bitonic_place_packed(xs, n, kappa, out_s, out_id);
+        else rank_place_packed(xs, n, kappa, out_s, out_id);
         return;
       }
     }
