@@ -296,9 +296,12 @@ SCORE_GROUPS = {GLV_F32: (4, 8, 16, 32), GLV_BF16: (4, 8, 16, 32), GLV_FP8_E4M3:
 
 GATHER_MODES = (0, 1, 2)  # registers, registers pipelined, bulk copies into shared memory
 
-# shared-memory carveout caps the autotuner tries, KB (0 = the driver's choice; 164 leaves
-# about 92 KB of the SM's 256 KB to L1 for the rows in flight)
-SCORE_CARVEOUTS = (0, 132, 164)
+# shared-memory carveout caps the autotuner tries, KB (164 leaves about 92 KB of the SM's
+# 256 KB to L1 for the rows in flight).  The driver's choice (0, still accepted by
+# glv_set_score_config) is not offered: alone it times within 0.1% of a cap, but when searches
+# run on two streams at once (HostSearchPipeline) it made the pipelined step slower than one
+# batch run alone (measured 2.96-3.02 ms against 1.79-1.84 ms with a cap, per 10k queries).
+SCORE_CARVEOUTS = (132, 164)
 
 # fused-call schedules, bit 0: planned work items (long lists cut into chunks), else one CTA per
 # query; bit 1: wide CTAs (512 threads, twice the keys on chip)
