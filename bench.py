@@ -222,9 +222,9 @@ KERNEL_SOURCES = tuple("paper_2410_22347_gb300/csrc/" + f for f in (
 # summaries and the capture commands are in profiles/.  A row whose hash no longer matches
 # the sources gives traffic null.
 TRAFFIC = {
-    ("graph-1M-d160", "bf16"): ("ce4ca9470160bcb9", (1.334986e9 + 4.890368e6) / (2000 * 2048)),
-    ("precision-10M-d128", "fp8"): ("ce4ca9470160bcb9", (1.318954240e9 + 13.160704e6) / (2000 * 4096)),
-    ("batching-2M-d192", "bf16"): ("ce4ca9470160bcb9", (2.940270e9 + 15.565056e6) / (4096 * 1868.338623046875)),
+    ("graph-1M-d160", "bf16"): ("7f7a0753cc7b76cb", (1.241791e+09 + 1.717197e+07) / (2000 * 2048)),
+    ("precision-10M-d128", "fp8"): ("7f7a0753cc7b76cb", (1.318681e+09 + 1.312358e+07) / (2000 * 4096)),
+    ("batching-2M-d192", "bf16"): ("7f7a0753cc7b76cb", (2.939976e+09 + 1.532518e+07) / (4096 * 1868.338623046875)),
 }
 
 

@@ -258,15 +258,17 @@ glv_status glv_score_topk(const float* Qp, int64_t nq, int32_t C, int32_t d, con
  * memory part of the SM's shared-memory / L1 split for the scoring kernels (0 = the
  * driver's choice, else 16..256 KB; ignored where one CTA would not fit under the cap): the
  * driver sizes that split for the kernel's full occupancy, and the L1 left over stages the
- * gathered rows in flight, so fewer CTAs with more L1 can be faster.  schedule (fused call
- * only), two bits: bit 0 set (1, the default) = the planned work items of glv_score_topk
- * (long lists cut into chunks, persistent CTAs), clear = one CTA per query, no plan (faster
- * when no list is long: no plan launch, no work counter); bit 1 set (2 or 3) = wide CTAs of
- * 512 threads instead of 256 (one query's staged projected views serve twice the warps, and
- * lists of up to 4096 candidates keep their scores on chip), offered with gather mode 0 and
- * the store type's two smaller lane counts (FP32 and BF16: 4, 8; FP8: 2, 4), else ignored.
- * All of these change only speed.  The fused call maps gather mode 2 to mode 0.  A choice that cannot serve a row width falls back to the default for
- * that width; glv_get_score_config reports the configuration used for rows of width d.
+ * gathered rows in flight, so fewer CTAs with more L1 can be faster.  schedule, three bits:
+ * bit 0 (fused call) set (1, the default) = the planned work items of glv_score_topk (long
+ * lists cut into chunks, persistent CTAs), clear = one CTA per query, no plan (faster when no
+ * list is long: no plan launch, no work counter); bit 1 (fused call) set = wide CTAs of 512
+ * threads instead of 256 (one query's staged projected views serve twice the warps, and lists
+ * of up to 4096 candidates keep their scores on chip), offered with gather mode 0 and the
+ * store type's two smaller lane counts (FP32 and BF16: 4, 8; FP8: 2, 4), else ignored; bit 2
+ * set = each candidate group asks L2 for the next candidate's row one iteration before loading
+ * it (prefetch; stand-alone scoring and 256-thread fused CTAs, ignored by wide ones).  All of these change only speed.  The fused
+ * call maps gather mode 2 to mode 0.  A choice that cannot serve a row width falls back to the
+ * default for that width; glv_get_score_config reports the configuration used for rows of width d.
  * Process-wide setting.  Errors: GLV_ERR_INVALID_ARG for an unknown dt, lane count, mode,
  * carveout or schedule.
  * ------------------------------------------------------------------------------------- */

@@ -24,7 +24,7 @@ CACHE = os.environ.get("GLV_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"
 
 def _key(dt: int, d: int, C: int, mean_len: float) -> str:
     name = torch.cuda.get_device_name()
-    return f"v6|{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
+    return f"v7|{name}|dt{dt}|d{d}|C{C}|L{int(round(mean_len, -1))}"
 
 
 def _load_cache() -> dict:

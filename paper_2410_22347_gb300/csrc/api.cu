@@ -63,6 +63,7 @@ static glv_status fill_score_args(ScoreArgs& a, const float* Qp, int64_t nq, int
   a.tail = (int)(bytes - (int64_t)(nch - 1) * 16);
   a.splits = 1;
   a.sbs = nch;
+  a.prefetch = 0;
   return GLV_OK;
 }
 

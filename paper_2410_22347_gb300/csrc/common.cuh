@@ -67,6 +67,9 @@ GLV_DEV void prefetch_l2_bulk(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Hint: bring the 128-byte line holding p into L2 (no register, no completion to wait for).
+GLV_DEV void prefetch_l2_line(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Ids as unsigned keys that grow as the (signed) id shrinks: ties between equal scores go to
 // the smaller id, negative (invalid) ids included, in every selection path.
 GLV_DEV uint32_t id_rank(int32_t id) { return ~((uint32_t)id ^ 0x80000000u); }

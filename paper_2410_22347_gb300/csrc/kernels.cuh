@@ -22,6 +22,7 @@ struct ScoreArgs {
   int tail;    // bytes of data in the last chunk (16 = full)
   int splits;  // CTAs per query (set by the launcher)
   int sbs;     // float4 stride between the sub-blocks of a projected-query row (set by the launcher)
+  int prefetch;  // 1: ask L2 for the next candidate's row one iteration ahead (set by the launcher)
 };
 
 // Shared-memory layout of a projected-query row (see dot_chunk in score_dev.cuh): EPC/4

@@ -53,7 +53,7 @@ static std::mutex g_cfg_mu;
 static ScoreConfig g_cfg[3] = {{0, 0, 0, 1}, {0, 0, 0, 1}, {0, 0, 0, 1}};  // G = 0: library default
 
 bool set_score_config(int dt, int G, int mode, int carve_kb, int sched) {
-  if (dt < 0 || dt > 2 || mode < 0 || mode > 2 || sched < 0 || sched > 3) return false;
+  if (dt < 0 || dt > 2 || mode < 0 || mode > 2 || sched < 0 || sched > 7) return false;
   const bool ok = (G == 0) || G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32;
   if (!ok) return false;
   if (carve_kb != 0 && (carve_kb < 16 || carve_kb > 256)) return false;
@@ -92,7 +92,7 @@ ScoreConfig resolve_config(int dt, int nch) {
     case GLV_BF16: wide_ok = wide_group_supported<GLV_BF16>(c.G); break;
     default: wide_ok = wide_group_supported<GLV_FP8_E4M3>(c.G); break;
   }
-  if ((c.sched & 2) && (!wide_ok || c.mode != 0)) c.sched &= 1;
+  if ((c.sched & 2) && (!wide_ok || c.mode != 0)) c.sched &= ~2;
   return c;
 }
 
@@ -127,6 +127,7 @@ cudaError_t launch_score(const ScoreArgs& a0, int dt, int64_t nq, int num_sms, c
   dim3 grid((unsigned)nq, (unsigned)splits);
   int RB = 0;
   const ScoreConfig cfg = with_rings(resolve_config(dt, a.nch), a.C, a.qstride, false, a.nch, 0, &RB);
+  a.prefetch = (cfg.sched & 4) ? 1 : 0;
   switch (dt) {
     case GLV_F32: return launch_score_dt<GLV_F32>(a, grid, RB, cfg, st);
     case GLV_BF16: return launch_score_dt<GLV_BF16>(a, grid, RB, cfg, st);
@@ -269,7 +270,8 @@ cudaError_t launch_score_topk(const ScoreArgs& a0, int dt, int64_t nq, int64_t n
   // wide CTAs keep twice the keys on chip; where that does not fit, the 256-thread kernel runs
   if ((cfg.sched & 2) &&
       score_smem(a.C, a.qstride, true, 0, 0, a.nch, kappa, fused_cache(kWideThreads)).total() > kScoreSmemLimit)
-    cfg.sched &= 1;
+    cfg.sched &= ~2;
+  a.prefetch = (cfg.sched & 4) ? 1 : 0;
   const ChunkPlan plan = topk_plan_layout(plan_ws, nq);
   unsigned grid = (unsigned)nq;  // one CTA per query
   if (cfg.sched & 1) {

@@ -280,7 +280,7 @@ GLV_DEV void finish_row(const ScoreArgs& a, const RowLoad<DT, G, NCH, PIPE>& r, 
   }
 }
 
-template <int DT, int G, int NCH, bool PIPE, bool TAIL, class Sink>
+template <int DT, int G, int NCH, bool PIPE, bool TAIL, bool PF, class Sink>
 GLV_DEV void score_range_t(const ScoreArgs& a, const float* qs, int64_t b0, int64_t b1, Sink& sink) {
   constexpr int GPW = kWarp / G;
   const int lane = threadIdx.x & (kWarp - 1);
@@ -293,7 +293,26 @@ GLV_DEV void score_range_t(const ScoreArgs& a, const float* qs, int64_t b0, int6
   // the id of the next candidate is loaded one iteration ahead, so the row loads of an
   // iteration do not wait for an id round trip
   int64_t id_next = (base + g < b1) ? (int64_t)__ldg(a.ids + base + g) : 0;
-  if constexpr (!PIPE) {
+  if constexpr (!PIPE && PF) {
+    // prefetch: ids are loaded two iterations ahead, and each lane of a group asks L2 for one
+    // 128-byte line of the next candidate's row one iteration before its loads (a hint: it
+    // holds no register and no L1 slot, so the SM keeps twice the row bytes on their way --
+    // faster where part of the store sits in L2, slower where every row comes from DRAM; the
+    // autotuner chooses)
+    int64_t id_next2 = (base + step + g < b1) ? (int64_t)__ldg(a.ids + base + step + g) : 0;
+    const int row_bytes = a.nch * 16;
+    for (; base < b1; base += step) {
+      const int64_t p = base + g;
+      const int64_t id = id_next;
+      id_next = id_next2;
+      id_next2 = (p + 2 * step < b1) ? (int64_t)__ldg(a.ids + p + 2 * step) : 0;
+      if (p + step < b1 && id_next >= 0 && id_next < a.N && gl * 128 < row_bytes)
+        prefetch_l2_line(a.Xred + id_next * a.row_stride + gl * 128);
+      RowLoad<DT, G, NCH, PIPE> r;
+      load_row(a, r, p, b1, id, gl);
+      finish_row<DT, G, NCH, PIPE, TAIL>(a, r, qs, gl, sw, sink);
+    }
+  } else if constexpr (!PIPE) {
     for (; base < b1; base += step) {
       const int64_t p = base + g;
       const int64_t id = id_next;
@@ -325,12 +344,25 @@ GLV_DEV void score_range_t(const ScoreArgs& a, const float* qs, int64_t b0, int6
 }
 
 // Rows whose data end inside a 16-byte chunk (d * element bytes not a multiple of 16) need the
-// bytes past the data masked in that chunk; the loop is compiled twice and the kernel-uniform
-// choice is made once, so rows that end on a chunk boundary pay nothing for it.
-template <int DT, int G, int NCH, bool PIPE, class Sink>
+// bytes past the data masked in that chunk, and the L2 prefetch of the next row is an option;
+// the loop is compiled in three forms and the kernel-uniform choice is made once, so rows that
+// end on a chunk boundary pay nothing for the mask and launches without the prefetch nothing
+// for it.  (Rows with a partial last chunk take the form without the prefetch.)
+// ALLOW_PF: whether the kernel carries the prefetch form at all (the 512-thread fused kernel
+// does not: the third form of the loop cost its other forms 13-18% through code generation).
+template <int DT, int G, int NCH, bool PIPE, bool ALLOW_PF = true, class Sink>
 GLV_DEV void score_range(const ScoreArgs& a, const float* qs, int64_t b0, int64_t b1, Sink sink) {
-  if (a.tail < 16) score_range_t<DT, G, NCH, PIPE, true>(a, qs, b0, b1, sink);
-  else score_range_t<DT, G, NCH, PIPE, false>(a, qs, b0, b1, sink);
+  if (a.tail < 16) {
+    score_range_t<DT, G, NCH, PIPE, true, false>(a, qs, b0, b1, sink);  // (rare: no prefetch form)
+    return;
+  }
+  if constexpr (ALLOW_PF && !PIPE) {
+    if (a.prefetch) {
+      score_range_t<DT, G, NCH, PIPE, false, true>(a, qs, b0, b1, sink);
+      return;
+    }
+  }
+  score_range_t<DT, G, NCH, PIPE, false, false>(a, qs, b0, b1, sink);
 }
 
 // Default lanes per candidate per store type: 8 for FP32 and BF16 rows, 4 for FP8 rows (the

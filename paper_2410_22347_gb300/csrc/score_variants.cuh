@@ -197,10 +197,10 @@ __global__ void __launch_bounds__(TPB, fused_min_blocks_t(DT, MODE, NCH, TPB))
     const int64_t b0 = s_rec[cur].b0, b1 = b0 + s_rec[cur].len;
     if (b1 - b0 <= kCache) {
       auto sink = [kc, b0](int64_t p, float s) { kc[p - b0] = score_key(s); };
-      score_range<DT, G, NCH, MODE == 1>(a, qs, b0, b1, sink);
+      score_range<DT, G, NCH, MODE == 1, TPB == kScoreThreads>(a, qs, b0, b1, sink);
     } else {
       auto sink = [scores](int64_t p, float s) { scores[p] = s; };
-      score_range<DT, G, NCH, MODE == 1>(a, qs, b0, b1, sink);
+      score_range<DT, G, NCH, MODE == 1, TPB == kScoreThreads>(a, qs, b0, b1, sink);
     }
     if (threadIdx.x == 0) cp_async_wait_all();
     __syncthreads();

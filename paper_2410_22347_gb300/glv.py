@@ -304,8 +304,9 @@ GATHER_MODES = (0, 1, 2)  # registers, registers pipelined, bulk copies into sha
 SCORE_CARVEOUTS = (132, 164)
 
 # fused-call schedules, bit 0: planned work items (long lists cut into chunks), else one CTA per
-# query; bit 1: wide CTAs (512 threads, twice the keys on chip)
-SCORE_SCHEDULES = (1, 0, 3, 2)
+# query; bit 1: wide CTAs (512 threads, twice the keys on chip); bit 2: L2 prefetch of the next
+# candidate's row
+SCORE_SCHEDULES = (1, 0, 3, 2, 5, 4, 7, 6)
 
 
 def glv_set_score_config(dt: int, lanes_per_candidate: int, gather_mode: int, smem_carveout_kb: int = 0,

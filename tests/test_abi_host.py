@@ -172,7 +172,7 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert setc(1, 4, 1, 300, 1) == INV     # above the SM's shared memory
     assert setc(1, 3, 0, 0, 1) == INV       # lanes per candidate not a power of two
     assert setc(1, 4, 3, 0, 1) == INV       # no gather mode 3
-    assert setc(1, 4, 0, 0, 4) == INV       # schedules are 0..3
+    assert setc(1, 4, 0, 0, 8) == INV       # schedules are 0..7
     assert setc(1, 4, 0, 0, 3) == 0         # wide CTAs, planned items
     assert getc(1, 160, *ref) == 0 and (g.value, m.value, h.value) == (4, 0, 3)
     assert setc(1, 16, 0, 0, 3) == 0        # no wide kernel with 16 lanes: the bit is dropped

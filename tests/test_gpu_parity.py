@@ -641,7 +641,7 @@ def test_score_config_roundtrip(glv):
         glv.glv_set_score_config(glv.GLV_BF16, 4, 2, 164, 0)
         assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (4, 2, 164, 0)
         with pytest.raises(glv.GlvError):
-            glv.glv_set_score_config(glv.GLV_BF16, 4, 0, 0, 4)
+            glv.glv_set_score_config(glv.GLV_BF16, 4, 0, 0, 8)
         glv.glv_set_score_config(glv.GLV_BF16, 8, 0, 132, 2)
         assert glv.glv_get_score_config(glv.GLV_BF16, 160) == (8, 0, 132, 2)
         glv.glv_set_score_config(glv.GLV_BF16, 8, 1, 0, 3)  # no wide kernel with pipelined loads
@@ -664,7 +664,7 @@ def test_carveout_and_schedule_change_no_result(glv, dt_name, kappa):
     dt = glv.DTYPES[dt_name]
     try:
         for carve in (0, 164):
-            for sched in (1, 0, 3, 2):
+            for sched in (1, 0, 3, 2, 5, 6):
                 glv.glv_set_score_config(dt, 0, 0, carve, sched)
                 test_score_topk_fused_matches_separate(glv, dt_name, 700, kappa)
     finally:
